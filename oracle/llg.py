@@ -1,0 +1,104 @@
+"""Effective field, LLG right-hand side, Euler step, energy (FP64; test
+infrastructure only).
+
+Readings of the paper's Sec. 2 (each listed with its reason in the design
+notes):
+* Eq. (1)'s exchange term repeats M_x three times; read as the sum over
+  M_x, M_y, M_z.
+* Eq. (3)/(4) omit mu0, which Eq. (5) carries; H_exch = 2A/(mu0 Ms^2) lap M
+  is the dimensionally consistent field (A/m) from Eq. (1)-(2).
+* Eq. (5) is read from Eq. (1): H_anis = -(2 Ku/(mu0 Ms^2)) (0, M_y, M_z),
+  an easy x axis.
+* Eq. (6) with ``gamma`` = gamma_0 in m/(A s) and H in A/m: the mu0 inside
+  Eq. (6) is absorbed into gamma_0.
+* Exchange boundary: free (Neumann): a missing neighbour is the cell itself.
+* Integrator: forward Euler (Table 1 caption) with every term at M^n, then
+  renormalisation |M| = Ms.
+"""
+import numpy as np
+
+from .tensor import MU0
+from .demag import demag_fft
+
+
+def h_exchange(M, cell, Ms, A):
+    """Eq. (4) for all three components, Neumann boundaries."""
+    pref = 2.0 * A / (MU0 * Ms * Ms)
+    P = np.pad(M, ((0, 0), (1, 1), (1, 1), (1, 1)), mode="edge")
+    c = P[:, 1:-1, 1:-1, 1:-1]
+    dx, dy, dz = cell
+    lap = ((P[:, 1:-1, 1:-1, 2:] - 2 * c + P[:, 1:-1, 1:-1, :-2]) / dx ** 2
+           + (P[:, 1:-1, 2:, 1:-1] - 2 * c + P[:, 1:-1, :-2, 1:-1]) / dy ** 2
+           + (P[:, 2:, 1:-1, 1:-1] - 2 * c + P[:, :-2, 1:-1, 1:-1]) / dz ** 2)
+    return pref * lap
+
+
+def h_anisotropy(M, Ms, Ku):
+    """Uniaxial anisotropy with easy axis x, from Eq. (1)-(2)."""
+    pref = -2.0 * Ku / (MU0 * Ms * Ms)
+    H = np.zeros_like(M, dtype=np.float64)
+    H[1] = pref * M[1]
+    H[2] = pref * M[2]
+    return H
+
+
+def h_effective(M, cell, Ms, A, Ku, H_ext, H_demag):
+    """Eq. (2): H_eff = H_exch + H_anis + H_demag + H_ext."""
+    H = h_exchange(M, cell, Ms, A) + h_anisotropy(M, Ms, Ku) + H_demag
+    return H + np.asarray(H_ext, np.float64).reshape(3, 1, 1, 1)
+
+
+def llg_rhs(M, H, Ms, alpha, gamma):
+    """Eq. (6): dM/dt = -g/(1+a^2) M x H - a g/((1+a^2) Ms) M x (M x H)."""
+    MxH = np.cross(M, H, axis=0)
+    MxMxH = np.cross(M, MxH, axis=0)
+    c = gamma / (1.0 + alpha * alpha)
+    return -c * MxH - (c * alpha / Ms) * MxMxH
+
+
+def euler_step(M, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
+    """One forward-Euler step of Eq. (6) with every field at M^n, followed by
+    renormalisation to |M| = Ms.  Returns (M^{n+1}, H_demag(M^n))."""
+    Hd = demag_fft(M, Kt, L)
+    H = h_effective(M, cell, Ms, A, Ku, H_ext, Hd)
+    Mn = M + dt * llg_rhs(M, H, Ms, alpha, gamma)
+    Mn = Mn * (Ms / np.sqrt(np.sum(Mn * Mn, axis=0)))
+    return Mn, Hd
+
+
+def run_euler(M, nsteps, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
+    for _ in range(nsteps):
+        M, _ = euler_step(M, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)
+    return M
+
+
+def energy_terms(M, H_demag, cell, Ms, A, Ku, H_ext):
+    """Eq. (1) integrated over the sample, in joules:
+    (total, exchange, anisotropy, demag, Zeeman).
+
+    Exchange is the link sum A V sum_links |m_i - m_j|^2 / delta^2 (m =
+    M/Ms), the discrete form of A (grad m)^2 that matches Eq. (4) with
+    Neumann boundaries."""
+    dx, dy, dz = cell
+    V = dx * dy * dz
+    m = M / Ms
+    ex = 0.0
+    for axis, d in ((3, dx), (2, dy), (1, dz)):
+        diff = np.diff(m, axis=axis)
+        ex += np.sum(diff * diff) / (d * d)
+    ex *= A * V
+    an = Ku * V * np.sum(M[1] ** 2 + M[2] ** 2) / (Ms * Ms)
+    de = -0.5 * MU0 * V * np.sum(H_demag * M)
+    ze = -MU0 * V * np.sum(np.asarray(H_ext, np.float64).reshape(3, 1, 1, 1) * M)
+    return np.array([ex + an + de + ze, ex, an, de, ze])
+
+
+def macrospin_closed_form(theta0, phi0, H, alpha, gamma, t):
+    """Exact solution of Eq. (6) for one moment in a static field H along +z
+    (no other torque): the polar angle obeys
+    tan(theta/2) = tan(theta0/2) exp(-alpha gamma H t / (1 + alpha^2)) and the
+    azimuth advances as phi0 + gamma H t / (1 + alpha^2)."""
+    w = gamma * H / (1.0 + alpha * alpha)
+    theta = 2.0 * np.arctan(np.tan(theta0 / 2.0) * np.exp(-alpha * w * t))
+    phi = phi0 + w * t
+    return theta, phi

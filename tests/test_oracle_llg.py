@@ -1,0 +1,135 @@
+"""Pins of the FP64 field / LLG / energy oracle (oracle/llg.py) against
+closed forms: Neumann-Laplacian eigenmodes, the energy-field identity
+H = -(1/(mu0 V)) dE/dM, the exact macrospin solution of Eq. (6), |M| = Ms,
+and monotone energy decay for alpha > 0."""
+import numpy as np
+import pytest
+
+from oracle import tensor as T
+from oracle import demag as D
+from oracle import llg as L
+from paper_1406_7459_gb300 import inputs
+
+MU0 = T.MU0
+
+
+def test_uniform_state_has_no_exchange_field():
+    M = inputs.uniform_m((5, 4, 3), 8.6e5, (0.3, 0.4, 0.5)).astype(np.float64)
+    H = L.h_exchange(M, (5e-9, 4e-9, 3e-9), 8.6e5, 1.3e-11)
+    assert np.max(np.abs(H)) < 1e-6
+
+
+@pytest.mark.parametrize("q", [(1, 0, 0), (2, 1, 0), (3, 2, 1)])
+def test_neumann_cosine_modes_are_exact_eigenvectors(q):
+    grid, cell = (8, 6, 4), (5e-9, 4e-9, 3e-9)
+    Ms, A = 8.6e5, 1.3e-11
+    nx, ny, nz = grid
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx),
+                          indexing="ij")
+    mode = (np.cos(np.pi * q[0] * (i + 0.5) / nx)
+            * np.cos(np.pi * q[1] * (j + 0.5) / ny)
+            * np.cos(np.pi * q[2] * (k + 0.5) / nz))
+    M = np.stack([mode, 0.5 * mode, -mode])
+    lam = sum((2 - 2 * np.cos(np.pi * qa / na)) / d ** 2
+              for qa, na, d in zip(q, grid, cell))
+    H = L.h_exchange(M, cell, Ms, A)
+    expect = -(2 * A / (MU0 * Ms * Ms)) * lam * M
+    assert np.max(np.abs(H - expect)) < 1e-10 * np.max(np.abs(expect))
+
+
+def _energy(M, cell, Ms, A, Ku, Hext, Kt, Lp):
+    Hd = D.demag_fft(M, Kt, Lp)
+    return L.energy_terms(M, Hd, cell, Ms, A, Ku, Hext)[0]
+
+
+def test_effective_field_is_minus_energy_gradient():
+    """dE = -mu0 V sum H_eff . dM for every term of Eq. (1)/(2), checked by
+    central differences in a random direction (M off the sphere is fine)."""
+    grid, cell = (6, 5, 3), (5e-9, 4e-9, 3e-9)
+    Ms, A, Ku, Hext = 8.6e5, 1.3e-11, 4e4, (1e4, -2e4, 3e4)
+    V = np.prod(cell)
+    M = inputs.random_unit_m(grid, Ms, seed=11).astype(np.float64)
+    dM = inputs.random_unit_m(grid, Ms, seed=12).astype(np.float64)
+    Lp = D.default_lengths(grid)
+    Kt = D.kernel_spectrum(T.tensor_octant(grid, cell), Lp)
+    eps = 1e-4
+    dE = (_energy(M + eps * dM, cell, Ms, A, Ku, Hext, Kt, Lp)
+          - _energy(M - eps * dM, cell, Ms, A, Ku, Hext, Kt, Lp)) / (2 * eps)
+    H = L.h_effective(M, cell, Ms, A, Ku, Hext, D.demag_fft(M, Kt, Lp))
+    expect = -MU0 * V * np.sum(H * dM)
+    assert abs(dE - expect) < 1e-8 * abs(expect)
+
+
+def test_exchange_link_energy_identity():
+    grid, cell = (7, 5, 2), (5e-9, 4e-9, 3e-9)
+    Ms, A = 8.6e5, 1.3e-11
+    M = inputs.random_unit_m(grid, Ms, seed=5).astype(np.float64)
+    E = L.energy_terms(M, np.zeros_like(M), cell, Ms, A, 0.0, (0, 0, 0))
+    Hx = L.h_exchange(M, cell, Ms, A)
+    assert abs(E[1] + 0.5 * MU0 * np.prod(cell) * np.sum(Hx * M)) < 1e-12 * abs(E[1])
+
+
+def test_llg_rhs_is_perpendicular_to_m():
+    grid = (4, 3, 2)
+    M = inputs.random_unit_m(grid, 8.6e5, seed=1).astype(np.float64)
+    H = 1e5 * inputs.random_unit_m(grid, 1.0, seed=2).astype(np.float64)
+    f = L.llg_rhs(M, H, 8.6e5, 0.3, 2.211e5)
+    assert np.max(np.abs(np.sum(f * M, axis=0))) < 1e-9 * np.max(np.abs(f)) * 8.6e5
+
+
+def _macrospin_run(dt, t_end, theta0, phi0, Hz, alpha, gamma, Ms):
+    cell = (3e-9, 3e-9, 3e-9)          # cube: demag field is parallel to M
+    grid = (1, 1, 1)
+    Lp = D.default_lengths(grid)
+    Kt = D.kernel_spectrum(T.tensor_octant(grid, cell), Lp)
+    M = Ms * np.array([np.sin(theta0) * np.cos(phi0),
+                       np.sin(theta0) * np.sin(phi0),
+                       np.cos(theta0)]).reshape(3, 1, 1, 1)
+    n = int(round(t_end / dt))
+    M = L.run_euler(M, n, dt, cell, Ms, 1.3e-11, 0.0, alpha, gamma,
+                    (0.0, 0.0, Hz), Kt, Lp)
+    return M.reshape(3) / Ms
+
+
+def test_macrospin_matches_closed_form_with_first_order_error():
+    theta0, phi0, Hz, alpha, gamma, Ms = 1.2, 0.3, 2e5, 0.1, 2.211e5, 8.6e5
+    t_end = 2e-10
+    th, ph = L.macrospin_closed_form(theta0, phi0, Hz, alpha, gamma, t_end)
+    exact = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    errs = []
+    for dt in (4e-14, 2e-14, 1e-14):
+        m = _macrospin_run(dt, t_end, theta0, phi0, Hz, alpha, gamma, Ms)
+        errs.append(np.linalg.norm(m - exact))
+    assert errs[-1] < 5e-3
+    for a, b in zip(errs[:-1], errs[1:]):
+        assert 1.8 < a / b < 2.2, errs        # forward Euler: O(dt)
+
+
+def test_renormalisation_keeps_norm_and_energy_decays():
+    grid, cell = (8, 8, 2), (5e-9, 5e-9, 3e-9)
+    Ms, A, Ku, alpha, gamma = 8.6e5, 1.3e-11, 5e2, 0.5, 2.211e5
+    Hext = (1e4, 2e3, 0.0)
+    Lp = D.default_lengths(grid)
+    Kt = D.kernel_spectrum(T.tensor_octant(grid, cell), Lp)
+    M = inputs.random_unit_m(grid, Ms, seed=1).astype(np.float64)
+    E_prev = _energy(M, cell, Ms, A, Ku, Hext, Kt, Lp)
+    for _ in range(60):
+        M, _ = L.euler_step(M, 1e-13, cell, Ms, A, Ku, alpha, gamma, Hext, Kt, Lp)
+        assert np.max(np.abs(np.sqrt(np.sum(M * M, axis=0)) - Ms)) < 1e-9 * Ms
+        E = _energy(M, cell, Ms, A, Ku, Hext, Kt, Lp)
+        assert E <= E_prev + 1e-12 * abs(E_prev)
+        E_prev = E
+
+
+def test_undamped_energy_drift_is_first_order():
+    grid, cell = (6, 6, 1), (5e-9, 5e-9, 3e-9)
+    Ms, A, Ku, gamma = 8.6e5, 1.3e-11, 0.0, 2.211e5
+    Lp = D.default_lengths(grid)
+    Kt = D.kernel_spectrum(T.tensor_octant(grid, cell), Lp)
+    M0 = inputs.perturbed_m(grid, Ms, seed=4, amplitude=0.3).astype(np.float64)
+    E0 = _energy(M0, cell, Ms, A, Ku, (0, 0, 0), Kt, Lp)
+    drift = []
+    for dt, n in ((2e-15, 100), (1e-15, 200)):
+        M = L.run_euler(M0, n, dt, cell, Ms, A, Ku, 0.0, gamma, (0, 0, 0), Kt, Lp)
+        drift.append(abs(_energy(M, cell, Ms, A, Ku, (0, 0, 0), Kt, Lp) - E0))
+    assert 1.6 < drift[0] / drift[1] < 2.4, drift
