@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the demag + LLG step on the 256x256x4 film.
+
+Workload (the size-sweep film at 256x256x4): 4 nm cubic cells, Ms 8.6e5 A/m,
+A 1.3e-11 J/m, Ku 5e2 J/m^3 (easy x), alpha 0.02, gamma_0 2.211e5, uniform
++x start, H_ext 2.5e4 A/m at 170 degrees in the xy plane, Euler dt 5e-14 s.
+Synthetic data: the paper's own workload (muMAG standard problem 3) is not
+reproduced; the seeded film stands in for it.
+
+A step is one forward-Euler step (x R2C -> y/z FFT + tensor product ->
+x C2R + field + LLG + Euler), i.e. one demag evaluation plus the update.
+Every timed step starts with a cold L2: a 256 MiB buffer is overwritten
+before it (outside the CUDA-event bracket).  `value` is cells*steps/s over
+all ranks (replicas only: each rank integrates its own film; there is no
+data-path collective).
+
+--impl reference times the FP64 numpy oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = (256, 256, 4)
+METRIC = "cells·steps/s and demag evals/s at 256×256×4; HBM GB/s fraction; vs oracle"
+UNIT = "cells·steps/s"
+FLUSH_BYTES = 256 << 20
+
+
+def workload():
+    from paper_1406_7459_gb300 import inputs
+    w = dict(inputs.FILM_SWEEP)
+    w["grid"] = GRID
+    return w
+
+
+def config_dict():
+    w = workload()
+    return {
+        "workload": "film 256x256x4, 4 nm cells, Ku 5e2 easy x, alpha 0.02, uniform +x start, "
+                    "H_ext 2.5e4 A/m at 170 deg, Euler dt 5e-14 s",
+        "grid": list(GRID), "cell_m": list(w["cell"]), "padded": [512, 512, 8],
+        "l2": "flushed before every timed step (256 MiB write)",
+        "parallelism": "replicas",
+    }
+
+
+def algorithmic_bytes(grid):
+    """Bytes each pass must move at least once (FP32 SoA M, complex64
+    half-spectrum X = (Lx/2+1)*ny*nz per component, FP32 tensor octant
+    Ks = (Lx/2+1)(Ly/2+1)(Lz/2+1) bins x 6)."""
+    nx, ny, nz = grid
+    L = [1 if n == 1 else 2 * n for n in grid]     # power-of-two grids here
+    N = nx * ny * nz
+    X = (L[0] // 2 + 1) * ny * nz
+    Ks = (L[0] // 2 + 1) * (L[1] // 2 + 1) * (L[2] // 2 + 1)
+    return {"pass1": 12 * N + 24 * X, "pass2": 48 * X + 24 * Ks, "pass3": 24 * X + 24 * N,
+            "step": 36 * N + 96 * X + 24 * Ks, "demag": 24 * N + 96 * X + 24 * Ks}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        loaded = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_rate(seconds_budget=15.0, max_steps=None):
+    """Time the FP64 numpy oracle's Euler step on the same workload, on a
+    bounded number of steps; returns (cells*steps/s, steps, seconds)."""
+    from oracle import tensor as T, demag as D, llg as L
+    from paper_1406_7459_gb300 import inputs
+    w = workload()
+    Lp = D.default_lengths(GRID)
+    Kt = D.kernel_spectrum(T.tensor_octant(GRID, w["cell"]), Lp)
+    M = inputs.uniform_m(GRID, w["Ms"], w["start"]).astype(np.float64)
+    args = (w["dt"], w["cell"], w["Ms"], w["A"], w["Ku"], w["alpha"], w["gamma"], w["H_ext"], Kt, Lp)
+    M, _ = L.euler_step(M, *args)                    # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        M, _ = L.euler_step(M, *args)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget or (max_steps and n >= max_steps):
+            break
+    N = GRID[0] * GRID[1] * GRID[2]
+    return N * n / el, n, el
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return 0
+    budget = min(120.0, max(10.0, 0.1 * args.steps))
+    rate, n, el = oracle_rate(seconds_budget=budget, max_steps=args.steps)
+    N = GRID[0] * GRID[1] * GRID[2]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(),
+        "cpu_baseline": {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
+                         "sample": "%d FP64 numpy Euler steps of the full 256x256x4 film (%.1f s; numpy "
+                                   "FFT single-threaded)" % (n, el)},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args, rank, ws):
+    import torch
+    from paper_1406_7459_gb300 import mm, inputs
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    w = workload()
+    N = GRID[0] * GRID[1] * GRID[2]
+    ctx = mm.mm_create(GRID, w["cell"], w["Ms"], w["A"], w["Ku"], w["alpha"], w["gamma"])
+    mm.mm_set_field(ctx, w["H_ext"])
+    M0 = inputs.uniform_m(GRID, w["Ms"], w["start"]).reshape(-1)
+    mm.mm_set_m(ctx, torch.from_numpy(M0).cuda())
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    dt = w["dt"]
+    K, W = args.steps, args.warmup
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    mm.mm_step(ctx, max(W, 3), dt)                   # warm-up (graph capture)
+    torch.cuda.synchronize()
+    # keep the clocks busy ~1 s so the sampler sees the load
+    t_end = time.perf_counter() + 1.0
+    while time.perf_counter() < t_end:
+        mm.mm_step(ctx, 50, dt)
+        torch.cuda.synchronize()
+
+    # --- timed region: K steps, cold L2 before each, events around each step
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    for s in range(K):
+        flush.fill_(float(s))
+        starts[s].record()
+        mm.mm_step(ctx, 1, dt)
+        ends[s].record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    t_local = sum(step_ms) / 1e3
+    mm.mm_sync(ctx)
+
+    # --- per-pass durations (same cold-L2 protocol), for the roofline
+    reps = min(K, 200)
+    p1, p2, p3 = mm.mm_time_passes(ctx, reps, dt, flush)
+
+    # --- demag evaluations per second (cold L2 per evaluation)
+    Md = torch.empty(3 * N, device="cuda")
+    mm.mm_get_m(ctx, Md)
+    Hd = torch.empty_like(Md)
+    de_s = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    de_e = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for s in range(reps):
+        flush.fill_(float(s))
+        de_s[s].record()
+        mm.mm_demag_field(ctx, Md, Hd)
+        de_e[s].record()
+    torch.cuda.synchronize()
+    demag_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(de_s, de_e))
+
+    # --- steady state without flushing (L2-resident working set), context only
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    mm.mm_step(ctx, K, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    warm_ms = e0.elapsed_time(e1) / K
+
+    # --- end to end through the C ABI with host buffers
+    Mh = torch.from_numpy(M0.copy()).pin_memory()
+    Mo = torch.empty_like(Mh).pin_memory()
+    ke = min(K, 200)
+    e2e_t = 0.0
+    for s in range(ke):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mm.mm_set_m(ctx, Mh.numpy())
+        mm.mm_step(ctx, 1, dt)
+        mm.mm_get_m(ctx, Mo.numpy())
+        e2e_t += time.perf_counter() - t0
+    clocks = sampler.stop()
+
+    t_max = max_over_ranks(t_local, ws)
+    e2e_max = max_over_ranks(e2e_t, ws)
+    value = ws * N * K / t_max
+    by = algorithmic_bytes(GRID)
+    peak, peak_kind = measured_peaks()
+    passes = {"pass1_x_r2c": p1, "pass2_yz_plane": p2, "pass3_x_c2r_llg": p3}
+    dom = max(passes, key=passes.get)
+    dom_bytes = {"pass1_x_r2c": by["pass1"], "pass2_yz_plane": by["pass2"], "pass3_x_c2r_llg": by["pass3"]}[dom]
+    achieved = dom_bytes / (passes[dom] * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(dom)
+        except Exception:
+            traffic = None
+    step_ms_mean = 1e3 * t_max / K
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": step_ms_mean, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": config_dict(),
+        "demag_evals_per_s": ws * 1e3 / demag_ms,
+        "step_hbm": {"algorithmic_bytes": by["step"], "gbs": by["step"] / (step_ms_mean * 1e-3) / 1e9,
+                     "frac": by["step"] / (step_ms_mean * 1e-3) / 1e9 / peak},
+        "pass_ms": passes,
+        "steady_state_l2_resident": {"ms_per_step": warm_ms, "cells_steps_per_s": ws * N / (warm_ms * 1e-3)},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic},
+        "gpu_launches": 3 * K,
+        "clocks": clocks,
+        "e2e": {"value": ws * N * ke / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
+                "d2h_bytes_per_step": 12 * N},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, n, el = oracle_rate(seconds_budget=args.cpu_seconds)
+        line["cpu_baseline"] = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
+                                "sample": "%d FP64 numpy Euler steps of the same 256x256x4 film (%.1f s, "
+                                          "numpy FFT single-threaded)" % (n, el)}
+    mm.mm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, ws = dist_setup()
+    if args.impl == "reference":
+        rc = run_reference(args, rank, ws)
+    else:
+        rc = run_gpu(args, rank, ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

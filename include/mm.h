@@ -1,0 +1,186 @@
+/*
+ * mm.h -- C ABI of the GB300 (sm_103a) demag + LLG hot path.
+ *
+ * The library implements the per-step loop of a finite-difference
+ * micromagnetic solver (Zhu, "Speedup of Micromagnetic Simulations with C++
+ * AMP on Graphics Processing Units"):
+ *   - the demagnetising field as the zero-padded FFT convolution of M with
+ *     the demag tensor (Sec. 2, Eqs. (7)-(13); Sec. 3, Eqs. (14)-(16)),
+ *   - the effective field H_eff = H_exch + H_anis + H_demag + H_ext
+ *     (Eqs. (2)-(5)), the LLG right-hand side (Eq. (6)) and a forward-Euler
+ *     step (Table 1 caption) followed by renormalisation to |M| = Ms,
+ *   - the energy of Eq. (1).
+ *
+ * Conventions shared by every call
+ *   Grid      nx x ny x nz cells, zero-indexed i, j, k (Sec. 2).
+ *   Layout    M and H are three SoA planes of float32 (x, y, z components),
+ *             each nx*ny*nz long, x fastest: element (c, i, j, k) sits at
+ *             c*N + i + nx*(j + ny*k), N = nx*ny*nz.
+ *   Units     SI: M, H in A/m; cell sizes in m; A in J/m; Ku in J/m^3;
+ *             gamma = gamma_0 in m/(A s) (mu0 absorbed, e.g. 2.211e5);
+ *             dt in s; energies in J.  mu0 = 4 pi 1e-7.
+ *   Pointers  The caller owns every pointer it passes.  Arguments named
+ *             *_dev must be device memory of the context's GPU.  Arguments
+ *             documented as "host or device" may be either (the copy uses
+ *             unified addressing).  The library owns its own device buffers
+ *             (tensor spectrum, FFT workspace, M ping-pong) and frees them in
+ *             mm_destroy.
+ *   Streams   All GPU work of a context is issued on the stream given to
+ *             mm_create (NULL = the CUDA legacy default stream) and is
+ *             asynchronous unless a call says it synchronises.
+ *   Errors    Every call returns MM_OK (0) or a negative MM_E* code; no C++
+ *             exception crosses the ABI.  mm_last_error() gives a message for
+ *             the last failing call on the calling thread.  A failing call
+ *             leaves the context's state unchanged, except MM_ENONFINITE,
+ *             which leaves the offending state in place for inspection.
+ *   Threads   A context may be used from one thread at a time.
+ */
+#ifndef MM_H
+#define MM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MM_OK = 0,
+    MM_EINVAL = -1,       /* bad grid, cell, material value or null pointer */
+    MM_ENOMEM = -2,       /* device allocation failed                         */
+    MM_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed      */
+    MM_ENONFINITE = -4,   /* a step produced a non-finite magnetisation       */
+    MM_ETIMEOUT = -5,     /* a bounded device-side wait gave up               */
+    MM_EUNSUPPORTED = -6  /* a size outside the supported plan limits         */
+};
+
+typedef struct mm_ctx mm_ctx;
+
+/*
+ * mm_create -- build a solver context; the tensor set-up happens here, once
+ * (Sec. 3: the tensor FFT "carried out at the beginning of simulation").
+ *
+ *   out     receives the new context (set to NULL on failure).
+ *   grid    {nx, ny, nz}, each >= 1.
+ *   cell    {dx, dy, dz} in m, each > 0.
+ *   Ms      saturation magnetisation, A/m, > 0 (Sec. 2).
+ *   A       exchange constant, J/m, >= 0 (Eq. (1), (3)).
+ *   Ku      uniaxial anisotropy constant, J/m^3, easy axis x (Eq. (1), (5)).
+ *   alpha   damping, >= 0 (Eq. (6)).
+ *   gamma   gamma_0 in m/(A s), > 0 (Eq. (6)).
+ *   cuda_stream  cudaStream_t to issue work on, or NULL.
+ *
+ * Set-up computes the cell-averaged (Newell) demag tensor in FP64 on the GPU
+ * (closed form near the source, Gauss-Legendre cell average far away), its
+ * transform on the zero-padded box (padded length per axis: 2n when n is a
+ * power of two, else the smallest 2^a 3^b 5^c >= 2n - 1; 1 when n = 1), and
+ * stores the real, octant-symmetric spectrum in FP32.  The initial M is
+ * uniform +x and H_ext = 0.  Synchronises the stream.
+ * Returns MM_EINVAL, MM_EUNSUPPORTED (padded length > 4096 on an axis or
+ * a working set beyond shared-memory plan limits), MM_ENOMEM or MM_ECUDA.
+ */
+int mm_create(mm_ctx **out, const int grid[3], const double cell[3],
+              double Ms, double A, double Ku, double alpha, double gamma,
+              void *cuda_stream);
+
+/* mm_destroy -- free every resource of ctx.  NULL-safe.  Synchronises. */
+int mm_destroy(mm_ctx *ctx);
+
+/* mm_set_field -- uniform external (Zeeman) field H_ext in A/m (Eq. (1),
+ * (2)); applies to later steps.  H_ext: 3 doubles, host memory. */
+int mm_set_field(mm_ctx *ctx, const double H_ext[3]);
+
+/* mm_set_m -- copy a magnetisation state into the context (Sec. 3: the
+ * initial conditions are the only host-to-device input).  M: 3*N float32,
+ * host or device.  Used as given: the caller supplies |M| = Ms. */
+int mm_set_m(mm_ctx *ctx, const float *M);
+
+/* mm_get_m -- copy the current magnetisation out.  M: 3*N float32, host or
+ * device.  Synchronises when M is host memory. */
+int mm_get_m(mm_ctx *ctx, float *M);
+
+/*
+ * mm_demag_field -- H_demag of M by the padded FFT convolution:
+ * forward x R2C (pruned), forward y/z FFT (pruned), 3x3 real-tensor product
+ * (Eq. (13)/(15)), inverse z/y (pruned), inverse x C2R keeping i < nx
+ * (Eq. (10)/(16)).  M_dev, H_dev: 3*N float32 device arrays, must not
+ * overlap.  Does not touch the context's own M.  Asynchronous.
+ */
+int mm_demag_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
+
+/*
+ * mm_effective_field -- H_eff = H_exch + H_anis + H_demag + H_ext of M
+ * (Eqs. (2)-(5)); exchange with free (Neumann) boundaries.  M_dev, H_dev:
+ * 3*N float32 device arrays, must not overlap.  Asynchronous.
+ */
+int mm_effective_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
+
+/*
+ * mm_step -- n forward-Euler steps of Eq. (6) of size dt on the resident M:
+ * M <- Ms * (M + dt f(M)) / |M + dt f(M)|, every field term at M^n.  Each
+ * step is three kernels (x R2C; per-kx-plane y/z FFT + tensor product +
+ * inverse y/z; inverse x C2R fused with exchange, anisotropy, Zeeman, LLG,
+ * Euler and renormalisation) replayed from CUDA graphs.  n >= 0, dt > 0.
+ * Asynchronous: a non-finite result is reported by mm_sync / mm_energy.
+ */
+int mm_step(mm_ctx *ctx, int n, double dt);
+
+/*
+ * mm_energy -- the energy of Eq. (1) for the current M, summed in FP64:
+ * E[0] total, E[1] exchange (link sum A V sum |m_i - m_j|^2 / delta^2),
+ * E[2] anisotropy, E[3] demag (-1/2 mu0 V sum H_d . M), E[4] Zeeman, in J.
+ * E: 5 doubles, host memory.  Synchronises; returns MM_ENONFINITE if any
+ * earlier step produced a non-finite value.
+ */
+int mm_energy(mm_ctx *ctx, double E[5]);
+
+/* mm_sync -- wait for the context's stream; MM_ENONFINITE if any step since
+ * mm_create / mm_set_m produced a non-finite magnetisation. */
+int mm_sync(mm_ctx *ctx);
+
+/* mm_last_error -- message for the last nonzero status returned on the
+ * calling thread ("" if none).  ctx may be NULL.  The string stays valid
+ * until the next call on this thread. */
+const char *mm_last_error(const mm_ctx *ctx);
+
+/*
+ * mm_plan_info -- the padded lengths and the decomposition chosen by
+ * mm_create.  L: {Lx, Ly, Lz} (may be NULL).  Returns the number of kernel
+ * launches per step (>= 3) or a negative error code.
+ */
+int mm_plan_info(const mm_ctx *ctx, int L[3]);
+
+/*
+ * mm_tensor_octant -- recompute the FP64 real-space demag tensor N (K = -N)
+ * on the non-negative offset octant, as used by set-up: out holds
+ * 6*nx*ny*nz doubles, component-major (xx, xy, xz, yy, yz, zz), then
+ * offset (i, j, k) at i + nx*(j + ny*k).  Host or device.  Synchronises.
+ * Diagnostic; not on the per-step path.
+ */
+int mm_tensor_octant(mm_ctx *ctx, double *out);
+
+/*
+ * mm_kernel_spectrum -- copy the stored FP32 spectrum of K = -N, already
+ * divided by Lx*Ly*Lz (the inverse-FFT normalisation is folded in), on the
+ * octant 0..L/2 of each axis: out holds (Lx/2+1)*(Lz/2+1)*(Ly/2+1)*6 floats
+ * laid out [kx][kz][ky][component].  Host or device.  Synchronises.
+ * Diagnostic; not on the per-step path.
+ */
+int mm_kernel_spectrum(mm_ctx *ctx, float *out);
+
+/*
+ * mm_time_passes -- diagnostic timing of the three step kernels.  Runs
+ * `reps` Euler steps of size dt on the resident M (advancing it exactly as
+ * mm_step does), launching the passes directly and bracketing each with CUDA
+ * events on the context's stream.  When flush is non-NULL, flush_bytes of
+ * that device buffer are overwritten before every step so that each step
+ * starts with a cold L2 (the memset is outside the bracketed passes).
+ * ms[3] (host) receives the mean duration in milliseconds of pass 1 (x R2C),
+ * pass 2 (y/z FFT + tensor product + inverse y/z) and pass 3 (x C2R + field +
+ * LLG + Euler).  Synchronises.  Returns MM_EINVAL for reps < 1 or null ms.
+ */
+int mm_time_passes(mm_ctx *ctx, int reps, double dt, void *flush, unsigned long long flush_bytes,
+                   float ms[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

@@ -1,0 +1,501 @@
+// mm_api.cu -- the C ABI of include/mm.h: argument checks, the plan, device
+// buffers, CUDA-graph replay of the step and the error channel.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/mm.h"
+#include "mm_internal.h"
+
+using namespace mmk;
+
+static thread_local char g_err[512];
+
+static int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CU(expr)                                                                               \
+    do {                                                                                       \
+        cudaError_t _e = (expr);                                                               \
+        if (_e != cudaSuccess)                                                                 \
+            return fail(_e == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(_e), __FILE__, __LINE__);                    \
+    } while (0)
+
+struct mm_ctx {
+    int grid[3];
+    double cell[3];
+    double Ms, A, Ku, alpha, gamma;
+    double Hext[3];
+    cudaStream_t stream;
+    cudaStream_t cap;          // private stream used only for graph capture
+    int device;
+    Geom g;
+    Launch l;
+    float* Kt = nullptr;
+    float2* S = nullptr;
+    float* Mbuf[2] = {nullptr, nullptr};
+    int cur = 0;
+    float* H = nullptr;
+    int* flag = nullptr;
+    double* partials = nullptr;
+    double* Edev = nullptr;
+    float2* tw = nullptr;      // twiddles of x, y, z back to back
+    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+    double step_dt[2] = {0, 0};
+    unsigned long long step_ver[2] = {0, 0};
+    unsigned long long ver = 1;   // bumped when H_ext changes
+    bool use_graphs = true;
+};
+
+// ------------------------------------------------------------------ plan --
+static bool smooth235(int n) {
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Padded length of an axis with n cells: any L >= 2n-1 gives the exact
+// linear convolution; take 2n when n is a power of two (the paper's choice),
+// otherwise the smallest 2^a 3^b 5^c >= 2n-1; n = 1 needs no padding.
+static int padded_length(int n) {
+    if (n == 1) return 1;
+    if ((n & (n - 1)) == 0) return 2 * n;
+    int L = 2 * n - 1;
+    while (!smooth235(L)) ++L;
+    return L;
+}
+
+static bool make_axis_plan(int L, AxisPlan* p) {
+    memset(p, 0, sizeof(*p));
+    p->L = L;
+    int n = L, a = 0;
+    while (n % 2 == 0) { n /= 2; ++a; }
+    int st = (a + 3) / 4;               // stages for the power-of-two part
+    for (int s = 0; s < st; ++s) {      // spread the bits evenly, <= 4 each
+        const int bits = a / st + (s < a % st ? 1 : 0);
+        p->rad[p->nst++] = 1 << bits;
+    }
+    while (n % 5 == 0) { n /= 5; p->rad[p->nst++] = 5; }
+    while (n % 3 == 0) { n /= 3; p->rad[p->nst++] = 3; }
+    return n == 1 && p->nst <= kMaxStages;
+}
+
+static int build_plan(mm_ctx* c) {
+    Geom& g = c->g;
+    Launch& l = c->l;
+    g.nx = c->grid[0];
+    g.ny = c->grid[1];
+    g.nz = c->grid[2];
+    g.N = g.nx * g.ny * g.nz;
+    g.Lx = padded_length(g.nx);
+    g.Ly = padded_length(g.ny);
+    g.Lz = padded_length(g.nz);
+    if (g.Lx > kMaxLen || g.Ly > kMaxLen || g.Lz > kMaxLen)
+        return fail(MM_EUNSUPPORTED, "padded length exceeds %d", kMaxLen);
+    g.Hx = g.Lx / 2 + 1;
+    g.Hy = g.Ly / 2 + 1;
+    g.Hz = g.Lz / 2 + 1;
+    g.Jst = g.ny;
+    if (!make_axis_plan(g.Lx, &g.px) || !make_axis_plan(g.Ly, &g.py) || !make_axis_plan(g.Lz, &g.pz))
+        return fail(MM_EUNSUPPORTED, "no radix plan for padded lengths %d %d %d", g.Lx, g.Ly, g.Lz);
+    if (g.nz > kMaxPlaneNz || !plane_supported_lz(g.Lz))
+        return fail(MM_EUNSUPPORTED, "nz = %d: only nz <= %d is planned", g.nz, kMaxPlaneNz);
+
+    // Each pass holds its lines plus a Stockham ping-pong scratch in shared
+    // memory (fft_lines); `g*` is the number of lines per scratch group.
+    const size_t smem_cap = 227 * 1024;
+    const size_t lx_bytes = (size_t)padded_len(g.Lx) * sizeof(float2);
+    const size_t ly_bytes = (size_t)padded_len(g.Ly) * sizeof(float2);
+    // pass 1: R1/2 complex lines of Lx (+ as many scratch lines), <= ~64 KB
+    int lines1 = (int)(32768 / lx_bytes);
+    lines1 = lines1 < 1 ? 1 : (lines1 > 4 ? 4 : lines1);
+    l.r1 = 2 * lines1;
+    if (l.r1 > g.ny + (g.ny & 1)) l.r1 = g.ny + (g.ny & 1);
+    l.t1 = 256;
+    l.g1 = l.r1 / 2;
+    l.smem1 = (size_t)2 * (l.r1 / 2) * lx_bytes;
+    // pass 3: 3 * R3/2 lines of Lx (+ scratch)
+    int pairs3 = (int)(32768 / (3 * lx_bytes));
+    pairs3 = pairs3 < 1 ? 1 : (pairs3 > 2 ? 2 : pairs3);
+    l.r3 = 2 * pairs3;
+    if (l.r3 > g.ny + (g.ny & 1)) l.r3 = g.ny + (g.ny & 1);
+    l.t3 = 256;
+    l.g3 = 3 * l.r3 / 2;
+    l.smem3 = (size_t)2 * l.g3 * lx_bytes;
+    // pass 2: one kx plane of 3*nz lines of Ly, scratch for g2 of them
+    const int nl2 = 3 * g.nz;
+    l.t2 = (nl2 * g.Ly >= 4096) ? 512 : 256;
+    const size_t plane_bytes = (size_t)nl2 * ly_bytes;
+    if (plane_bytes + ly_bytes > smem_cap)
+        return fail(MM_EUNSUPPORTED, "kx plane of %zu bytes exceeds shared memory", plane_bytes);
+    size_t fit = (smem_cap - plane_bytes) / ly_bytes;
+    l.g2 = (int)(fit < (size_t)nl2 ? fit : (size_t)nl2);
+    l.smem2 = plane_bytes + (size_t)l.g2 * ly_bytes;
+    if (l.smem1 > smem_cap || l.smem3 > smem_cap)
+        return fail(MM_EUNSUPPORTED, "x lines of %zu bytes exceed shared memory", lx_bytes);
+    return MM_OK;
+}
+
+static void host_twiddles(int L, float2* out) {
+    for (int m = 0; m < L; ++m) {
+        const double a = -2.0 * 3.14159265358979323846 * (double)m / (double)L;
+        out[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+}
+
+static LlgCoef make_coef(const mm_ctx* c, double dt) {
+    LlgCoef f;
+    const double Ms2 = c->Ms * c->Ms;
+    const double den = 1.0 + c->alpha * c->alpha;
+    f.Ms = (float)c->Ms;
+    f.pexch = (float)(2.0 * c->A / (kMu0 * Ms2));
+    f.panis = (float)(-2.0 * c->Ku / (kMu0 * Ms2));
+    f.c1 = (float)(-c->gamma / den);
+    f.c2 = (float)(-c->alpha * c->gamma / (den * c->Ms));
+    f.idx2 = (float)(1.0 / (c->cell[0] * c->cell[0]));
+    f.idy2 = (float)(1.0 / (c->cell[1] * c->cell[1]));
+    f.idz2 = (float)(1.0 / (c->cell[2] * c->cell[2]));
+    f.hx = (float)c->Hext[0];
+    f.hy = (float)c->Hext[1];
+    f.hz = (float)c->Hext[2];
+    f.dt = (float)dt;
+    return f;
+}
+
+static void release(mm_ctx* c) {
+    for (int p = 0; p < 2; ++p)
+        if (c->step_exec[p]) cudaGraphExecDestroy(c->step_exec[p]);
+    cudaFree(c->Kt);
+    cudaFree(c->S);
+    cudaFree(c->Mbuf[0]);
+    cudaFree(c->Mbuf[1]);
+    cudaFree(c->H);
+    cudaFree(c->flag);
+    cudaFree(c->partials);
+    cudaFree(c->Edev);
+    cudaFree(c->tw);
+    if (c->cap) cudaStreamDestroy(c->cap);
+}
+
+// ------------------------------------------------------------------ API --
+extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], double Ms, double A, double Ku,
+                         double alpha, double gamma, void* cuda_stream) {
+    g_err[0] = 0;
+    if (!out) return fail(MM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !cell) return fail(MM_EINVAL, "grid or cell is NULL");
+    for (int a = 0; a < 3; ++a) {
+        if (grid[a] < 1) return fail(MM_EINVAL, "grid[%d] = %d < 1", a, grid[a]);
+        if (!(cell[a] > 0.0) || !std::isfinite(cell[a])) return fail(MM_EINVAL, "cell[%d] must be > 0", a);
+    }
+    if (!(Ms > 0.0) || !std::isfinite(Ms)) return fail(MM_EINVAL, "Ms must be > 0");
+    if (!(A >= 0.0) || !std::isfinite(A)) return fail(MM_EINVAL, "A must be >= 0");
+    if (!std::isfinite(Ku)) return fail(MM_EINVAL, "Ku must be finite");
+    if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(MM_EINVAL, "alpha must be >= 0");
+    if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(MM_EINVAL, "gamma must be > 0");
+    if ((long long)grid[0] * grid[1] * grid[2] > (1LL << 28)) return fail(MM_EUNSUPPORTED, "grid too large");
+
+    mm_ctx* c = new (std::nothrow) mm_ctx();
+    if (!c) return fail(MM_ENOMEM, "host allocation failed");
+    for (int a = 0; a < 3; ++a) {
+        c->grid[a] = grid[a];
+        c->cell[a] = cell[a];
+        c->Hext[a] = 0.0;
+    }
+    c->Ms = Ms;
+    c->A = A;
+    c->Ku = Ku;
+    c->alpha = alpha;
+    c->gamma = gamma;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->use_graphs = !(getenv("MM_NO_GRAPHS") && getenv("MM_NO_GRAPHS")[0] == '1');
+    int rc = build_plan(c);
+    if (rc != MM_OK) {
+        delete c;
+        return rc;
+    }
+    rc = [&]() -> int {
+        CU(cudaGetDevice(&c->device));
+        CU(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        Geom& g = c->g;
+        const size_t N = (size_t)g.N;
+        CU(cudaMalloc(&c->Kt, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.Hz));
+        CU(cudaMalloc(&c->S, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
+        CU(cudaMalloc(&c->Mbuf[0], sizeof(float) * 3 * N));
+        CU(cudaMalloc(&c->Mbuf[1], sizeof(float) * 3 * N));
+        CU(cudaMalloc(&c->H, sizeof(float) * 3 * N));
+        CU(cudaMalloc(&c->flag, sizeof(int)));
+        CU(cudaMalloc(&c->partials, sizeof(double) * energy_partials_elems(g.N)));
+        CU(cudaMalloc(&c->Edev, sizeof(double) * 5));
+        CU(cudaMalloc(&c->tw, sizeof(float2) * (size_t)(g.Lx + g.Ly + g.Lz)));
+        {
+            float2* h = (float2*)malloc(sizeof(float2) * (size_t)(g.Lx + g.Ly + g.Lz));
+            if (!h) return fail(MM_ENOMEM, "host allocation failed");
+            host_twiddles(g.Lx, h);
+            host_twiddles(g.Ly, h + g.Lx);
+            host_twiddles(g.Lz, h + g.Lx + g.Ly);
+            cudaError_t e = cudaMemcpy(c->tw, h, sizeof(float2) * (size_t)(g.Lx + g.Ly + g.Lz),
+                                       cudaMemcpyHostToDevice);
+            free(h);
+            CU(e);
+        }
+        g.twx = c->tw;
+        g.twy = c->tw + g.Lx;
+        g.twz = c->tw + g.Lx + g.Ly;
+        g.Kt = c->Kt;
+        CU(configure_pass_kernels(g, c->l));
+
+        // tensor set-up in FP64
+        const int L[3] = {g.Lx, g.Ly, g.Lz};
+        double *Nd = nullptr, *w1 = nullptr, *w2 = nullptr;
+        const size_t wn = tensor_work_elems(c->grid, L);
+        cudaError_t e = cudaMalloc(&Nd, sizeof(double) * 6 * N);
+        if (e == cudaSuccess) e = cudaMalloc(&w1, sizeof(double) * wn);
+        if (e == cudaSuccess) e = cudaMalloc(&w2, sizeof(double) * wn);
+        if (e == cudaSuccess) e = tensor_octant_fp64(c->grid, c->cell, Nd, c->stream);
+        if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(Nd);
+        cudaFree(w1);
+        cudaFree(w2);
+        CU(e);
+
+        // initial state: uniform +x
+        float* h = (float*)malloc(sizeof(float) * 3 * N);
+        if (!h) return fail(MM_ENOMEM, "host allocation failed");
+        for (size_t i = 0; i < N; ++i) {
+            h[i] = (float)Ms;
+            h[N + i] = 0.f;
+            h[2 * N + i] = 0.f;
+        }
+        e = cudaMemcpy(c->Mbuf[0], h, sizeof(float) * 3 * N, cudaMemcpyHostToDevice);
+        free(h);
+        CU(e);
+        CU(cudaMemset(c->flag, 0, sizeof(int)));
+        CU(cudaDeviceSynchronize());
+        return MM_OK;
+    }();
+    if (rc != MM_OK) {
+        release(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return MM_OK;
+}
+
+extern "C" int mm_destroy(mm_ctx* c) {
+    if (!c) return MM_OK;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+    return MM_OK;
+}
+
+extern "C" int mm_set_field(mm_ctx* c, const double H_ext[3]) {
+    if (!c || !H_ext) return fail(MM_EINVAL, "null argument");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(H_ext[a])) return fail(MM_EINVAL, "H_ext must be finite");
+    for (int a = 0; a < 3; ++a) c->Hext[a] = H_ext[a];
+    c->ver++;
+    return MM_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int mm_set_m(mm_ctx* c, const float* M) {
+    if (!c || !M) return fail(MM_EINVAL, "null argument");
+    CU(cudaMemcpyAsync(c->Mbuf[c->cur], M, sizeof(float) * 3 * (size_t)c->g.N, cudaMemcpyDefault, c->stream));
+    CU(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    if (!is_device_ptr(M)) CU(cudaStreamSynchronize(c->stream));
+    return MM_OK;
+}
+
+extern "C" int mm_get_m(mm_ctx* c, float* M) {
+    if (!c || !M) return fail(MM_EINVAL, "null argument");
+    CU(cudaMemcpyAsync(M, c->Mbuf[c->cur], sizeof(float) * 3 * (size_t)c->g.N, cudaMemcpyDefault, c->stream));
+    if (!is_device_ptr(M)) CU(cudaStreamSynchronize(c->stream));
+    return MM_OK;
+}
+
+static int run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt, cudaStream_t s) {
+    const LlgCoef cf = make_coef(c, dt);
+    CU(launch_pass1(c->g, c->l, M, c->S, s));
+    CU(launch_plane(c->g, c->l, c->S, s));
+    CU(launch_pass3(c->g, c->l, cf, mode, c->S, M, out, c->flag, s));
+    return MM_OK;
+}
+
+static bool overlap(const float* a, const float* b, size_t n) { return a < b + n && b < a + n; }
+
+extern "C" int mm_demag_field(mm_ctx* c, const float* M, float* H) {
+    if (!c || !M || !H) return fail(MM_EINVAL, "null argument");
+    if (overlap(M, H, 3 * (size_t)c->g.N)) return fail(MM_EINVAL, "M and H overlap");
+    return run_passes(c, kModeDemag, M, H, 0.0, c->stream);
+}
+
+extern "C" int mm_effective_field(mm_ctx* c, const float* M, float* H) {
+    if (!c || !M || !H) return fail(MM_EINVAL, "null argument");
+    if (overlap(M, H, 3 * (size_t)c->g.N)) return fail(MM_EINVAL, "M and H overlap");
+    return run_passes(c, kModeHeff, M, H, 0.0, c->stream);
+}
+
+// Capture one step (M[p] -> M[1-p]) on the private stream into a graph.
+static int capture_step(mm_ctx* c, int p, double dt) {
+    if (c->step_exec[p]) {
+        cudaGraphExecDestroy(c->step_exec[p]);
+        c->step_exec[p] = nullptr;
+    }
+    CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, c->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+    if (rc != MM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    CU(e);
+    e = cudaGraphInstantiate(&c->step_exec[p], graph, 0);
+    cudaGraphDestroy(graph);
+    CU(e);
+    c->step_dt[p] = dt;
+    c->step_ver[p] = c->ver;
+    return MM_OK;
+}
+
+extern "C" int mm_step(mm_ctx* c, int n, double dt) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    if (n < 0) return fail(MM_EINVAL, "n must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
+    for (int s = 0; s < n; ++s) {
+        const int p = c->cur;
+        if (c->use_graphs) {
+            if (!c->step_exec[p] || c->step_dt[p] != dt || c->step_ver[p] != c->ver) {
+                int rc = capture_step(c, p, dt);
+                if (rc != MM_OK) return rc;
+            }
+            CU(cudaGraphLaunch(c->step_exec[p], c->stream));
+        } else {
+            int rc = run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, c->stream);
+            if (rc != MM_OK) return rc;
+        }
+        c->cur = 1 - p;
+    }
+    return MM_OK;
+}
+
+static int read_flag(mm_ctx* c) {
+    int f = 0;
+    CU(cudaMemcpy(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) return fail(MM_ENONFINITE, "a step produced a non-finite magnetisation");
+    return MM_OK;
+}
+
+extern "C" int mm_sync(mm_ctx* c) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    CU(cudaStreamSynchronize(c->stream));
+    return read_flag(c);
+}
+
+extern "C" int mm_energy(mm_ctx* c, double E[5]) {
+    if (!c || !E) return fail(MM_EINVAL, "null argument");
+    int rc = run_passes(c, kModeDemag, c->Mbuf[c->cur], c->H, 0.0, c->stream);
+    if (rc != MM_OK) return rc;
+    CU(energy_reduce_full(c->g, c->Ms, c->Hext, c->cell, c->A, c->Ku, c->Mbuf[c->cur], c->H, c->partials,
+                          c->Edev, c->stream));
+    double h[5];
+    CU(cudaMemcpyAsync(h, c->Edev, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    rc = read_flag(c);
+    if (rc != MM_OK) return rc;
+    for (int q = 0; q < 5; ++q) E[q] = h[q];
+    return MM_OK;
+}
+
+extern "C" const char* mm_last_error(const mm_ctx*) { return g_err; }
+
+extern "C" int mm_plan_info(const mm_ctx* c, int L[3]) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    if (L) {
+        L[0] = c->g.Lx;
+        L[1] = c->g.Ly;
+        L[2] = c->g.Lz;
+    }
+    return 3;
+}
+
+extern "C" int mm_tensor_octant(mm_ctx* c, double* out) {
+    if (!c || !out) return fail(MM_EINVAL, "null argument");
+    const size_t n = (size_t)6 * c->g.N;
+    double* Nd = nullptr;
+    CU(cudaMalloc(&Nd, sizeof(double) * n));
+    cudaError_t e = tensor_octant_fp64(c->grid, c->cell, Nd, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, Nd, sizeof(double) * n, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(Nd);
+    CU(e);
+    return MM_OK;
+}
+
+extern "C" int mm_kernel_spectrum(mm_ctx* c, float* out) {
+    if (!c || !out) return fail(MM_EINVAL, "null argument");
+    const size_t n = (size_t)6 * c->g.Hx * c->g.Hy * c->g.Hz;
+    CU(cudaMemcpyAsync(out, c->Kt, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return MM_OK;
+}
+
+extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsigned long long flush_bytes,
+                              float ms[3]) {
+    if (!c || !ms || reps < 1) return fail(MM_EINVAL, "null argument or reps < 1");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
+    cudaEvent_t ev[4];
+    for (int q = 0; q < 4; ++q) CU(cudaEventCreate(&ev[q]));
+    double acc[3] = {0, 0, 0};
+    int rc = MM_OK;
+    const LlgCoef cf = make_coef(c, dt);
+    for (int r = 0; r < reps && rc == MM_OK; ++r) {
+        rc = [&]() -> int {
+            const int p = c->cur;
+            if (flush) CU(cudaMemsetAsync(flush, r & 0xff, (size_t)flush_bytes, c->stream));
+            CU(cudaEventRecord(ev[0], c->stream));
+            CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
+            CU(cudaEventRecord(ev[1], c->stream));
+            CU(launch_plane(c->g, c->l, c->S, c->stream));
+            CU(cudaEventRecord(ev[2], c->stream));
+            CU(launch_pass3(c->g, c->l, cf, kModeStep, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag, c->stream));
+            CU(cudaEventRecord(ev[3], c->stream));
+            CU(cudaEventSynchronize(ev[3]));
+            for (int q = 0; q < 3; ++q) {
+                float t = 0.f;
+                CU(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
+                acc[q] += t;
+            }
+            c->cur = 1 - p;
+            return MM_OK;
+        }();
+    }
+    for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
+    if (rc != MM_OK) return rc;
+    for (int q = 0; q < 3; ++q) ms[q] = (float)(acc[q] / reps);
+    return MM_OK;
+}

@@ -1,0 +1,78 @@
+// mm_internal.h -- context, plan and launcher declarations shared by the
+// translation units of libmm.so.  Not part of the public ABI (include/mm.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "fft_device.cuh"
+
+namespace mmk {
+
+constexpr double kMu0 = 4.0e-7 * 3.14159265358979323846;   // exact SI value
+constexpr int kMaxLen = 4096;          // largest padded length per axis
+constexpr int kMaxPlaneNz = 8;         // fused y/z plane kernel handles nz <= 8
+
+// Geometry of the padded convolution.  Spectrum element (kx, c, k, j) of the
+// workspace S sits at ((kx*3 + c)*nz + k)*Jst + j: kx slowest, so one kx
+// plane (3*nz*ny complex) is contiguous for the plane kernel.
+struct Geom {
+    int nx, ny, nz, N;
+    int Lx, Ly, Lz;
+    int Hx, Hy, Hz;            // L/2 + 1: stored half-spectrum / octant extents
+    int Jst;                   // stride of j in S (= ny)
+    AxisPlan px, py, pz;
+    const float2* twx;         // W_Lx^m, m < Lx (FP32, from FP64)
+    const float2* twy;
+    const float2* twz;
+    const float* Kt;           // tensor spectrum [kx][kz'][ky'][6], scaled
+};
+
+// Field and LLG coefficients in FP32 (computed in FP64 on the host).
+struct LlgCoef {
+    float Ms;
+    float pexch;               // 2A / (mu0 Ms^2)
+    float panis;               // -2 Ku / (mu0 Ms^2)
+    float c1;                  // -gamma / (1 + alpha^2)
+    float c2;                  // -alpha gamma / ((1 + alpha^2) Ms)
+    float idx2, idy2, idz2;    // 1 / delta^2
+    float hx, hy, hz;          // H_ext
+    float dt;
+};
+
+// Launch shapes chosen at plan time.
+struct Launch {
+    int r1, t1, g1;            // pass 1: rows per tile, threads, line group
+    int t2, g2;                // pass 2 (plane): threads, line group
+    int r3, t3, g3;            // pass 3: rows per tile, threads, line group
+    size_t smem1, smem2, smem3;
+};
+
+enum Pass3Mode { kModeDemag = 0, kModeHeff = 1, kModeStep = 2 };
+
+// Launchers (demag_passes.cu).  All asynchronous on `s`.
+cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s);
+cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s);
+cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int mode, const float2* S,
+                         const float* M, float* out, int* flag, cudaStream_t s);
+cudaError_t configure_pass_kernels(const Geom& g, const Launch& l);
+bool plane_supported_lz(int Lz);
+typedef void (*PlaneFn)(Geom, int, float2*);
+PlaneFn plane_fn_small(int Lz);   // plane_small.cu
+PlaneFn plane_fn_mid(int Lz);     // plane_mid.cu
+PlaneFn plane_fn_large(int Lz);   // plane_large.cu
+
+// Tensor set-up (tensor_setup.cu).  Writes N (FP64 octant) and/or Kt.
+cudaError_t tensor_octant_fp64(const int grid[3], const double cell[3], double* N_dev, cudaStream_t s);
+cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
+                            double* work1, double* work2, cudaStream_t s);
+size_t tensor_work_elems(const int grid[3], const int L[3]);
+
+// Energy (energy.cu): E[0..4] into out_dev (5 doubles, device); partials is
+// device scratch of energy_partials_elems(N) doubles.
+size_t energy_partials_elems(int N);
+cudaError_t energy_reduce_full(const Geom& g, double Ms, const double Hext[3], const double cell[3], double A,
+                               double Ku, const float* M, const float* Hd, double* partials, double* out_dev,
+                               cudaStream_t s);
+
+}  // namespace mmk

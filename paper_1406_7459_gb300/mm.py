@@ -1,0 +1,200 @@
+"""ctypes binding of libmm.so with the C ABI's names (include/mm.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors (float32, contiguous, 3*N
+elements, SoA planes with x fastest); host arrays are numpy float32.  Each
+call raises ``MMError`` on a nonzero status.  There is no CPU fallback: if
+the library is missing, the first call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmm.so")
+
+MM_OK = 0
+MM_EINVAL = -1
+MM_ENOMEM = -2
+MM_ECUDA = -3
+MM_ENONFINITE = -4
+MM_ETIMEOUT = -5
+MM_EUNSUPPORTED = -6
+
+# every function declared in include/mm.h, with (restype, argtypes)
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_PROTOS = {
+    "mm_create": (_c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_c_int), ctypes.POINTER(_c_double),
+                           _c_double, _c_double, _c_double, _c_double, _c_double, _vp]),
+    "mm_destroy": (_c_int, [_vp]),
+    "mm_set_field": (_c_int, [_vp, ctypes.POINTER(_c_double)]),
+    "mm_set_m": (_c_int, [_vp, _vp]),
+    "mm_get_m": (_c_int, [_vp, _vp]),
+    "mm_demag_field": (_c_int, [_vp, _vp, _vp]),
+    "mm_effective_field": (_c_int, [_vp, _vp, _vp]),
+    "mm_step": (_c_int, [_vp, _c_int, _c_double]),
+    "mm_energy": (_c_int, [_vp, ctypes.POINTER(_c_double)]),
+    "mm_sync": (_c_int, [_vp]),
+    "mm_last_error": (ctypes.c_char_p, [_vp]),
+    "mm_plan_info": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
+    "mm_tensor_octant": (_c_int, [_vp, _vp]),
+    "mm_kernel_spectrum": (_c_int, [_vp, _vp]),
+    "mm_time_passes": (_c_int, [_vp, _c_int, _c_double, _vp, ctypes.c_ulonglong,
+                                ctypes.POINTER(ctypes.c_float)]),
+}
+
+_lib = None
+
+
+class MMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libmm error %d: %s" % (code, msg))
+        self.code = code
+
+
+def lib():
+    """Load libmm.so once; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def mm_last_error(ctx=None):
+    return lib().mm_last_error(ctx).decode()
+
+
+def _check(rc):
+    if rc < 0:
+        raise MMError(rc, mm_last_error())
+    return rc
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x, n=None, dtype=np.float32):
+    """Raw pointer of a torch tensor (any device) or a numpy array."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy array must be C-contiguous %s" % np.dtype(dtype))
+        if n is not None and x.size != n:
+            raise ValueError("expected %d elements, got %d" % (n, x.size))
+        return x.ctypes.data
+    import torch
+    want = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+    if x.dtype != want or not x.is_contiguous():
+        raise ValueError("tensor must be contiguous %s" % want)
+    if n is not None and x.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, x.numel()))
+    return x.data_ptr()
+
+
+class Context:
+    """Owned handle of an mm_ctx plus its sizes."""
+
+    def __init__(self, handle, grid):
+        self.handle = handle
+        self.grid = tuple(grid)
+        self.N = grid[0] * grid[1] * grid[2]
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.mm_destroy(h)
+
+
+def mm_create(grid, cell, Ms, A, Ku, alpha, gamma, stream=None):
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    c = (ctypes.c_double * 3)(*[float(v) for v in cell])
+    out = _vp()
+    _check(lib().mm_create(ctypes.byref(out), g, c, Ms, A, Ku, alpha, gamma, _vp(_stream_handle(stream))))
+    return Context(out, tuple(int(v) for v in grid))
+
+
+def mm_destroy(ctx):
+    h, ctx.handle = ctx.handle, None
+    if h:
+        _check(lib().mm_destroy(h))
+
+
+def mm_set_field(ctx, H_ext):
+    h = (ctypes.c_double * 3)(*[float(v) for v in H_ext])
+    _check(lib().mm_set_field(ctx.handle, h))
+
+
+def mm_set_m(ctx, M):
+    _check(lib().mm_set_m(ctx.handle, _vp(_ptr(M, 3 * ctx.N))))
+
+
+def mm_get_m(ctx, out):
+    _check(lib().mm_get_m(ctx.handle, _vp(_ptr(out, 3 * ctx.N))))
+    return out
+
+
+def mm_demag_field(ctx, M, H):
+    _check(lib().mm_demag_field(ctx.handle, _vp(_ptr(M, 3 * ctx.N)), _vp(_ptr(H, 3 * ctx.N))))
+    return H
+
+
+def mm_effective_field(ctx, M, H):
+    _check(lib().mm_effective_field(ctx.handle, _vp(_ptr(M, 3 * ctx.N)), _vp(_ptr(H, 3 * ctx.N))))
+    return H
+
+
+def mm_step(ctx, n, dt):
+    _check(lib().mm_step(ctx.handle, int(n), float(dt)))
+
+
+def mm_energy(ctx):
+    E = (ctypes.c_double * 5)()
+    _check(lib().mm_energy(ctx.handle, E))
+    return np.array(list(E))
+
+
+def mm_sync(ctx):
+    _check(lib().mm_sync(ctx.handle))
+
+
+def mm_plan_info(ctx):
+    L = (ctypes.c_int * 3)()
+    launches = _check(lib().mm_plan_info(ctx.handle, L))
+    return tuple(L), launches
+
+
+def mm_tensor_octant(ctx):
+    nx, ny, nz = ctx.grid
+    out = np.zeros((6, nz, ny, nx), np.float64)
+    _check(lib().mm_tensor_octant(ctx.handle, _vp(_ptr(out, None, np.float64))))
+    return out
+
+
+def mm_kernel_spectrum(ctx):
+    (Lx, Ly, Lz), _ = mm_plan_info(ctx)
+    out = np.zeros((Lx // 2 + 1, Lz // 2 + 1, Ly // 2 + 1, 6), np.float32)
+    _check(lib().mm_kernel_spectrum(ctx.handle, _vp(_ptr(out))))
+    return out
+
+
+def mm_time_passes(ctx, reps, dt, flush=None):
+    """Mean per-pass durations (ms) over `reps` steps; `flush` is an optional
+    torch CUDA tensor overwritten before each step."""
+    ms = (ctypes.c_float * 3)()
+    fptr = flush.data_ptr() if flush is not None else None
+    fbytes = flush.numel() * flush.element_size() if flush is not None else 0
+    _check(lib().mm_time_passes(ctx.handle, int(reps), float(dt), _vp(fptr), fbytes, ms))
+    return tuple(ms)
