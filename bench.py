@@ -116,7 +116,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
         loaded = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
@@ -210,7 +210,7 @@ def run_gpu(args, rank, ws):
     mm.mm_step(ctx, max(W, 3), dt)                   # warm-up (graph capture)
     torch.cuda.synchronize()
     # keep the clocks busy ~1 s so the sampler sees the load
-    t_end = time.perf_counter() + 1.0
+    t_end = time.perf_counter() + (0.0 if args.quick else 1.0)
     while time.perf_counter() < t_end:
         mm.mm_step(ctx, 50, dt)
         torch.cuda.synchronize()
@@ -305,7 +305,7 @@ def run_gpu(args, rank, ws):
         "e2e": {"value": ws * N * ke / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N},
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not (args.no_cpu_baseline or args.quick):
         rate, n, el = oracle_rate(seconds_budget=args.cpu_seconds)
         line["cpu_baseline"] = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
                                 "sample": "%d FP64 numpy Euler steps of the same 256x256x4 film (%.1f s, "
@@ -324,6 +324,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="no clock warm-up loop and no CPU baseline (deterministic launch list for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -164,26 +164,40 @@ bool plane_supported_lz(int Lz) { return plane_fn(Lz) != nullptr; }
 
 cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem1);
-    if (e != cudaSuccess) return e;
+    if (l.fx) {
+        e = cudaFuncSetAttribute(l.fx->p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.fx->s1);
+        for (int m = 0; m < 3 && e == cudaSuccess; ++m)
+            e = cudaFuncSetAttribute(l.fx->p3[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.fx->s3);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem1);
+        if (e != cudaSuccess) return e;
+        for (int m = 0; m < 3 && e == cudaSuccess; ++m)
+            e = cudaFuncSetAttribute(m == 0 ? k_pass3<kModeDemag> : m == 1 ? k_pass3<kModeHeff> : k_pass3<kModeStep>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem3);
+        if (e != cudaSuccess) return e;
+    }
+    if (l.fp) return cudaFuncSetAttribute(l.fp->pl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.fp->s2);
     PlaneFn pf = plane_fn(g.Lz);
     if (!pf) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem2);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_pass3<kModeDemag>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem3);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_pass3<kModeHeff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem3);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pass3<kModeStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem3);
+    return cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem2);
 }
 
 cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s) {
+    if (l.fx) {
+        l.fx->p1<<<3 * g.nz * (g.ny / l.fx->r1), l.fx->t1, l.fx->s1, s>>>(g, M, S);
+        return cudaGetLastError();
+    }
     const int ntj = (g.ny + l.r1 - 1) / l.r1;
     k_pass1<<<3 * g.nz * ntj, l.t1, l.smem1, s>>>(g, l.r1, l.g1, M, S);
     return cudaGetLastError();
 }
 
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s) {
+    if (l.fp) {
+        l.fp->pl<<<g.Hx, l.fp->t2, l.fp->s2, s>>>(g, S);
+        return cudaGetLastError();
+    }
     PlaneFn pf = plane_fn(g.Lz);
     if (!pf) return cudaErrorInvalidValue;
     pf<<<g.Hx, l.t2, l.smem2, s>>>(g, l.g2, S);
@@ -192,6 +206,10 @@ cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t
 
 cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int mode, const float2* S,
                          const float* M, float* out, int* flag, cudaStream_t s) {
+    if (l.fx) {
+        l.fx->p3[mode]<<<g.nz * (g.ny / l.fx->r3), l.fx->t3, l.fx->s3, s>>>(g, c, S, M, out, flag);
+        return cudaGetLastError();
+    }
     const int ntj = (g.ny + l.r3 - 1) / l.r3;
     const int grid = g.nz * ntj;
     switch (mode) {

@@ -1,0 +1,27 @@
+// fast_plane_nz2.cu -- instantiations of the power-of-two plane kernel
+// (pass 2) for nz = 2, ny = 16, 32, 64, 128, 256, 512, 1024.
+#include "fast_passes.cuh"
+
+namespace mmk {
+
+template <int NY>
+static void fill_plane(FastFns* f) {
+    f->pl = k_plane_fast<NY, 2>;
+    f->t2 = 6 * 2 * Fft2<NY>::G;
+    f->s2 = plane_fast_smem<NY, 2>();
+}
+
+bool fast_lookup_plane_nz2(int ny, FastFns* f) {
+    switch (ny) {
+        case 16: fill_plane<16>(f); return true;
+        case 32: fill_plane<32>(f); return true;
+        case 64: fill_plane<64>(f); return true;
+        case 128: fill_plane<128>(f); return true;
+        case 256: fill_plane<256>(f); return true;
+        case 512: fill_plane<512>(f); return true;
+        case 1024: fill_plane<1024>(f); return true;
+        default: return false;
+    }
+}
+
+}  // namespace mmk

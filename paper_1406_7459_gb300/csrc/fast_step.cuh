@@ -1,0 +1,340 @@
+// fast_step.cuh -- the two-kernel Euler step for power-of-two grids.
+//
+// Step n (spectrum S[p] of M^n already formed):
+//   K_A  k_plane_pdl   per kx plane: y FFT, z DFT, tensor product (Eq. (15)),
+//                      inverse z, inverse y, in place on S[p].
+//   K_B  k_xstep_pdl   per (layer, row pair): inverse x C2R (Eq. (16)), the
+//                      field and LLG update of Eqs. (2)-(6) with the Euler
+//                      step and renormalisation, and then the forward x R2C
+//                      (Eq. (14)) of the new rows into S[1-p], which is the
+//                      first pass of step n+1.
+// So a step is two kernels and M^{n+1} is never re-read for its transform.
+//
+// Both kernels are launched with programmatic dependent launch.  Before
+// `griddepcontrol.wait` each one only touches data that no kernel of the
+// previous step writes: K_A prefetches its tensor-spectrum slice and the
+// twiddles; K_B prefetches twiddles and its M^n tile (M^n was written two
+// launches earlier, and K_A does not trigger its dependents before it has
+// passed its own wait, which orders it after that writer).  Each kernel
+// triggers its dependents only after its last global store.
+#pragma once
+#include <cuda_pipeline.h>
+
+#include "fast_passes.cuh"
+
+namespace mmk {
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// 16-byte asynchronous copies global -> shared (both 16-byte aligned).
+__device__ __forceinline__ void copy16(void* dst, const void* src) { __pipeline_memcpy_async(dst, src, 16); }
+
+template <int a, int b> struct cmax { static constexpr int v = a > b ? a : b; };
+
+// ------------------------------------------------------------- K_A plane --
+template <int NY, int NZ> struct PlaneLayout {
+    using F = Fft2<NY>;
+    static constexpr int LY = 2 * NY, ZS = pzlen(2 * NY), NL = 3 * NZ;
+    static constexpr int HZ = (NZ == 1) ? 1 : NZ + 1;   // Lz/2 + 1
+    static constexpr int HY = NY + 1;
+    static constexpr int KT_FLOATS = HZ * HY * 6;
+    static constexpr int KT_C = (KT_FLOATS + 1) / 2;      // in float2 units
+    static constexpr int WORK = cmax<NL * ZS, 2 * NL * F::EX>::v;
+    static constexpr int TW_OFF = 0, KT_OFF = LY, WORK_OFF = LY + ((KT_C + 1) / 2) * 2;
+    static constexpr size_t BYTES = sizeof(float2) * (WORK_OFF + WORK);
+    static constexpr int THREADS = 2 * NL * F::G;
+};
+
+template <int NY, int NZ>
+__global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY, NZ>::THREADS <= 512) ? 2 : 1)
+    k_plane_pdl(Geom g, float2* __restrict__ S) {
+    using Lay = PlaneLayout<NY, NZ>;
+    using F = Fft2<NY>;
+    constexpr int P = F::P, Q = F::Q, G = F::G, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm + Lay::TW_OFF;
+    float* Ks = reinterpret_cast<float*>(sm + Lay::KT_OFF);
+    float2* zb = sm + Lay::WORK_OFF;
+    float2* ex = zb;                                      // aliases zb (barriers separate uses)
+    const int kx = blockIdx.x;
+
+    // prologue: constant data only
+    for (int i = threadIdx.x; i < LY / 2; i += blockDim.x) copy16(tw + 2 * i, g.twy + 2 * i);
+    const float* Kp = g.Kt + (size_t)kx * Lay::KT_FLOATS;
+    // the slice starts 8-byte aligned; copy it as float2 pairs through registers
+    for (int i = threadIdx.x; i < Lay::KT_FLOATS / 2; i += blockDim.x)
+        reinterpret_cast<float2*>(Ks)[i] = __ldg(reinterpret_cast<const float2*>(Kp) + i);
+    __pipeline_commit();
+    pdl_wait();
+
+    float2* plane = S + (size_t)kx * NL * g.Jst;
+    const int grp = threadIdx.x / G, t = threadIdx.x % G;
+    const int line = grp >> 1, h = grp & 1;
+    float2 v[P];
+    if (t < Q) {
+        const float2* src = plane + (size_t)line * g.Jst;
+#pragma unroll
+        for (int q = 0; q < P; ++q) v[q] = src[t + Q * q];
+    }
+    __pipeline_wait_prior(0);
+    __syncthreads();
+    // forward y (pruned input): odd half pre-multiplied by W_LY^j
+    if (t < Q) {
+        if (h) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) v[q] = cmul(v[q], tw[t + Q * q]);
+        }
+        F::stepA(v, t, tw, ex + grp * F::EX, false);
+    }
+    __syncthreads();
+    float2 w[Q];
+    if (t < P) F::stepB(w, t, ex + grp * F::EX, false);
+    __syncthreads();
+    if (t < P) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) zb[line * ZS + pz(2 * (t + P * q) + h)] = w[q];
+    }
+    __syncthreads();
+    for (int ky = threadIdx.x; ky < LY; ky += blockDim.x) {
+        float2 m[3][NZ];
+        const int e = pz(ky);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) m[c][k] = zb[(c * NZ + k) * ZS + e];
+        zconv_column<NZ>(m, Ks, Lay::HY, LY, ky, g.twz);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) zb[(c * NZ + k) * ZS + e] = m[c][k];
+    }
+    __syncthreads();
+    // inverse y (pruned output)
+    if (t < Q) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) v[q] = zb[line * ZS + pz(2 * (t + Q * q) + h)];
+    }
+    __syncthreads();
+    if (t < Q) F::stepA(v, t, tw, ex + grp * F::EX, true);
+    __syncthreads();
+    if (t < P) F::stepB(w, t, ex + grp * F::EX, true);
+    __syncthreads();
+    if (t < P) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int n = t + P * q;
+            float2 val = w[q];
+            if (h) val = cmul(val, cconj(tw[n]));
+            zb[line * ZS + pz(h * NY + n)] = val;
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
+        const int l = idx / NY, n = idx % NY;
+        plane[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + pz(n)], zb[l * ZS + pz(NY + n)]);
+    }
+    __syncthreads();
+    pdl_trigger();
+}
+
+// ------------------------------------------------------------- K_B xstep --
+template <int N, int R> struct XstepLayout {
+    using F = Fft2<N>;
+    static constexpr int L = 2 * N, H = N + 1, NL = 3 * R / 2, ZS = pzlen(2 * N);
+    static constexpr int MROWS = 3 * R + 2;                // rows of the M tile per component
+    static constexpr int TW_OFF = 0;
+    static constexpr int MT_OFF = L;                              // float2 units; floats: 3*MROWS*N
+    static constexpr int MT_C = 3 * MROWS * N / 2;
+    static constexpr int SB_OFF = MT_OFF + MT_C;                  // staged spectrum / new M rows
+    static constexpr int SB_C = cmax<3 * H * R, 3 * R * N / 2>::v;
+    static constexpr int W_OFF = SB_OFF + ((SB_C + 1) / 2) * 2;
+    static constexpr int W_C = cmax<cmax<2 * NL * F::EX, NL * L>::v, NL * ZS>::v;
+    static constexpr size_t BYTES = sizeof(float2) * (W_OFF + W_C);
+    static constexpr int THREADS = cmax<2 * NL * F::G, 128>::v;
+};
+
+template <int N, int R>
+__global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
+    k_xstep_pdl(Geom g, LlgCoef cf, const float2* __restrict__ S, float2* __restrict__ Snext,
+                const float* __restrict__ M, float* __restrict__ Mout, int* __restrict__ flag) {
+    using Lay = XstepLayout<N, R>;
+    using F = Fft2<N>;
+    constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm + Lay::TW_OFF;
+    float* Mt = reinterpret_cast<float*>(sm + Lay::MT_OFF);
+    float2* sb = sm + Lay::SB_OFF;
+    float* Mn = reinterpret_cast<float*>(sm + Lay::SB_OFF);     // new M rows, after sb is consumed
+    float2* wk = sm + Lay::W_OFF;
+    const int ntj = g.ny / R;
+    const int jt = blockIdx.x % ntj;
+    const int k = blockIdx.x / ntj;
+    const int j0 = jt * R;
+    const size_t Nc = (size_t)g.N;
+    const size_t plane_xy = (size_t)N * g.ny;
+
+    // prologue: twiddles and the M^n tile.  Tile rows per component:
+    // [0, R+2): layer k rows j0-1 .. j0+R (clamped: a missing neighbour
+    // row is the edge row itself, the free-boundary rule of Eq. (4));
+    // [R+2, 2R+2): layer k-1 rows j0..j0+R-1; [2R+2, 3R+2): layer k+1.
+    for (int i = threadIdx.x; i < L / 2; i += blockDim.x) copy16(tw + 2 * i, g.twx + 2 * i);
+    {
+        constexpr int CH = N / 4;                               // 16-byte chunks per row
+        const int km = k > 0 ? k - 1 : k, kp = k + 1 < g.nz ? k + 1 : k;
+        for (int idx = threadIdx.x; idx < 3 * Lay::MROWS * CH; idx += blockDim.x) {
+            const int ch = idx % CH;
+            const int row = (idx / CH) % Lay::MROWS;
+            const int c = idx / (CH * Lay::MROWS);
+            int kk = k, jj;
+            if (row < R + 2) {
+                jj = j0 - 1 + row;
+                jj = jj < 0 ? 0 : (jj >= g.ny ? g.ny - 1 : jj);
+            } else if (row < 2 * R + 2) {
+                kk = km;
+                jj = j0 + row - (R + 2);
+            } else {
+                kk = kp;
+                jj = j0 + row - (2 * R + 2);
+            }
+            copy16(Mt + ((size_t)c * Lay::MROWS + row) * N + 4 * ch,
+                   M + c * Nc + (size_t)kk * plane_xy + (size_t)jj * N + 4 * ch);
+        }
+    }
+    __pipeline_commit();
+    pdl_wait();
+    // staged half-spectrum of the H tile: sb[(c*H + kx)*R + r]
+    {
+        constexpr int RC = R / 2;                               // 16-byte chunks per (kx, c)
+        for (int idx = threadIdx.x; idx < 3 * H * RC; idx += blockDim.x) {
+            const int q = idx % RC;
+            const int rest = idx / RC;
+            const int kx = rest % H, c = rest / H;
+            copy16(sb + (size_t)(c * H + kx) * R + 2 * q,
+                   S + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * q);
+        }
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    __syncthreads();
+
+    const int grp = threadIdx.x / G, t = threadIdx.x % G;
+    const int line = grp >> 1, h = grp & 1;
+    const int lc = line / (R / 2), pr = line % (R / 2);
+    const bool fft_thread = grp < 2 * NL;
+    float2 v[P];
+    float2 w[Q];
+    // ---- inverse x: rebuild Z = A + iB on the full length from the half-spectrum
+    if (fft_thread && t < Q) {
+        const float2* base = sb + (size_t)lc * H * R + 2 * pr;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int kk = 2 * (t + Q * q) + h;
+            const bool low = kk <= N;
+            const int ks = low ? kk : L - kk;
+            float2 A = base[ks * R], B = base[ks * R + 1];
+            if (ks == 0 || ks == N) { A.y = 0.f; B.y = 0.f; }
+            v[q] = low ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+        }
+        F::stepA(v, t, tw, wk + grp * F::EX, true);
+    }
+    __syncthreads();
+    if (fft_thread && t < P) F::stepB(w, t, wk + grp * F::EX, true);
+    __syncthreads();
+    if (fft_thread && t < P) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int n = t + P * q;
+            float2 val = w[q];
+            if (h) val = cmul(val, cconj(tw[n]));
+            wk[line * L + h * N + n] = val;                     // ob[line][h][n]
+        }
+    }
+    __syncthreads();
+    // ---- field, LLG, Euler, renormalisation per cell; new rows to Mn
+    for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+        const int r = idx / N;
+        const int i = idx % N;
+        const int j = j0 + r;
+        float hd[3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const int ln = cc * (R / 2) + (r >> 1);
+            const float2 z = cadd(wk[ln * L + i], wk[ln * L + N + i]);
+            hd[cc] = (r & 1) ? z.y : z.x;
+        }
+        const int im = i > 0 ? i - 1 : i, ip = i + 1 < N ? i + 1 : i;
+        float m[3], hh[3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const float* T = Mt + (size_t)cc * Lay::MROWS * N;
+            const float* row = T + (r + 1) * N;
+            const float m0 = row[i];
+            const float lap = (row[ip] - 2.f * m0 + row[im]) * cf.idx2 +
+                              (T[(r + 2) * N + i] - 2.f * m0 + T[r * N + i]) * cf.idy2 +
+                              (T[(2 * R + 2 + r) * N + i] - 2.f * m0 + T[(R + 2 + r) * N + i]) * cf.idz2;
+            m[cc] = m0;
+            hh[cc] = hd[cc] + cf.pexch * lap;
+        }
+        (void)j;
+        hh[0] += cf.hx;
+        hh[1] += cf.panis * m[1] + cf.hy;
+        hh[2] += cf.panis * m[2] + cf.hz;
+        const float p0 = m[1] * hh[2] - m[2] * hh[1];
+        const float p1 = m[2] * hh[0] - m[0] * hh[2];
+        const float p2 = m[0] * hh[1] - m[1] * hh[0];
+        const float q0 = m[1] * p2 - m[2] * p1;
+        const float q1 = m[2] * p0 - m[0] * p2;
+        const float q2 = m[0] * p1 - m[1] * p0;
+        const float n0 = m[0] + cf.dt * (cf.c1 * p0 + cf.c2 * q0);
+        const float n1 = m[1] + cf.dt * (cf.c1 * p1 + cf.c2 * q1);
+        const float n2 = m[2] + cf.dt * (cf.c1 * p2 + cf.c2 * q2);
+        const float s = cf.Ms / sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+        const float o0 = n0 * s, o1 = n1 * s, o2 = n2 * s;
+        if (!(isfinite(o0) && isfinite(o1) && isfinite(o2))) atomicOr(flag, 1);
+        const size_t cell = (size_t)i + (size_t)N * ((size_t)j0 + r) + plane_xy * k;
+        Mout[cell] = o0;
+        Mout[Nc + cell] = o1;
+        Mout[2 * Nc + cell] = o2;
+        Mn[(0 * R + r) * N + i] = o0;
+        Mn[(1 * R + r) * N + i] = o1;
+        Mn[(2 * R + r) * N + i] = o2;
+    }
+    __syncthreads();
+    // ---- forward x of the new rows (first pass of the next step)
+    if (fft_thread && t < Q) {
+        const float* ra = Mn + (size_t)(lc * R + 2 * pr) * N;
+        const float* rb = ra + N;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int jx = t + Q * q;
+            v[q] = make_float2(ra[jx], rb[jx]);
+            if (h) v[q] = cmul(v[q], tw[jx]);
+        }
+        F::stepA(v, t, tw, wk + grp * F::EX, false);
+    }
+    __syncthreads();
+    if (fft_thread && t < P) F::stepB(w, t, wk + grp * F::EX, false);
+    __syncthreads();
+    if (fft_thread && t < P) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) wk[line * ZS + pz(2 * (t + P * q) + h)] = w[q];
+    }
+    __syncthreads();
+    // split each pair into the two rows' half-spectra and store to Snext
+    for (int idx = threadIdx.x; idx < 3 * H * (R / 2); idx += blockDim.x) {
+        const int q = idx % (R / 2);
+        const int rest = idx / (R / 2);
+        const int c = rest % 3, kx = rest / 3;
+        const float2* ln = wk + (c * (R / 2) + q) * ZS;
+        const float2 zk = ln[pz(kx)];
+        const float2 zm = ln[pz((L - kx) & (L - 1))];
+        const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
+                                     0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        *reinterpret_cast<float4*>(Snext + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * q) = o;
+    }
+    __syncthreads();
+    pdl_trigger();
+}
+
+}  // namespace mmk

@@ -1,0 +1,76 @@
+// fast_step_x.cu -- instantiations of the fused inverse-x + LLG + forward-x
+// kernel (second kernel of the power-of-two step) for nx = 16 ... 1024.
+#include "fast_step.cuh"
+
+namespace mmk {
+
+template <int N>
+static void fill_xstep(FastStepFns* f) {
+    constexpr int R = 2;
+    f->kb = k_xstep_pdl<N, R>;
+    f->rb = R;
+    f->tb = XstepLayout<N, R>::THREADS;
+    f->sb = XstepLayout<N, R>::BYTES;
+}
+
+bool fast_step_lookup_x(int nx, FastStepFns* f) {
+    switch (nx) {
+        case 16: fill_xstep<16>(f); return true;
+        case 32: fill_xstep<32>(f); return true;
+        case 64: fill_xstep<64>(f); return true;
+        case 128: fill_xstep<128>(f); return true;
+        case 256: fill_xstep<256>(f); return true;
+        case 512: fill_xstep<512>(f); return true;
+        case 1024: fill_xstep<1024>(f); return true;
+        default: return false;
+    }
+}
+
+}  // namespace mmk
+
+namespace mmk {
+
+cudaError_t configure_step_kernels(const FastStepFns& f) {
+    cudaError_t e = cudaFuncSetAttribute(f.ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sa);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f.kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sb);
+}
+
+static cudaLaunchConfig_t step_cfg(dim3 grid, int threads, size_t smem, cudaStream_t s, bool pdl,
+                                   cudaLaunchAttribute* attr) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cfg;
+}
+
+cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, float2* S, cudaStream_t s, bool pdl) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = step_cfg(dim3(g.Hx), f.ta, f.sa, s, pdl, attr);
+    return cudaLaunchKernelEx(&cfg, f.ka, g, S);
+}
+
+cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* S, float2* Snext,
+                          const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = step_cfg(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, pdl, attr);
+    return cudaLaunchKernelEx(&cfg, f.kb, g, c, S, Snext, M, Mout, flag);
+}
+
+// K_A then K_B; with `pdl` both carry the programmatic-serialisation launch
+// attribute so each may start while its predecessor drains (each kernel
+// waits on griddepcontrol before reading what the predecessor wrote).
+cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Snext,
+                            const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
+    cudaError_t e = launch_step_a(g, f, S, s, pdl);
+    if (e != cudaSuccess) return e;
+    return launch_step_b(g, f, c, S, Snext, M, Mout, flag, s, pdl);
+}
+
+}  // namespace mmk

@@ -57,6 +57,11 @@ struct mm_ctx {
     unsigned long long step_ver[2] = {0, 0};
     unsigned long long ver = 1;   // bumped when H_ext changes
     bool use_graphs = true;
+    FastFns fast;              // compile-time kernels (when the grid has them)
+    FastStepFns fs;            // two-kernel step (power-of-two grids)
+    bool has_fs = false;
+    float2* S2 = nullptr;      // second spectrum buffer of the two-kernel step
+    bool spec_valid = false;   // S[cur] (S or S2) holds the x half-spectrum of M[cur]
 };
 
 // ------------------------------------------------------------------ plan --
@@ -145,6 +150,32 @@ static int build_plan(mm_ctx* c) {
     l.smem2 = plane_bytes + (size_t)l.g2 * ly_bytes;
     if (l.smem1 > smem_cap || l.smem3 > smem_cap)
         return fail(MM_EUNSUPPORTED, "x lines of %zu bytes exceed shared memory", lx_bytes);
+
+    // Power-of-two grids use the compile-time kernels (same spectrum layout).
+    const char* nofast = getenv("MM_NO_FAST");
+    const bool allow_fast = !(nofast && nofast[0] == '1');
+    l.fx = nullptr;
+    l.fp = nullptr;
+    if (allow_fast) {
+        FastFns& f = c->fast;
+        if (fast_lookup_x(g.nx, &f) && g.ny % f.r1 == 0 && g.ny % f.r3 == 0 && f.s1 <= smem_cap &&
+            f.s3 <= smem_cap)
+            l.fx = &f;
+        bool pl = false;
+        switch (g.nz) {
+            case 1: pl = fast_lookup_plane_nz1(g.ny, &f); break;
+            case 2: pl = fast_lookup_plane_nz2(g.ny, &f); break;
+            case 4: pl = fast_lookup_plane_nz4(g.ny, &f); break;
+            case 8: pl = fast_lookup_plane_nz8(g.ny, &f); break;
+            default: break;
+        }
+        if (pl && f.s2 <= smem_cap) l.fp = &f;
+        FastStepFns& s = c->fs;
+        bool ok = fast_step_lookup_x(g.nx, &s);
+        ok = ok && (fast_step_lookup_plane_a(g.ny, g.nz, &s) || fast_step_lookup_plane_b(g.ny, g.nz, &s));
+        ok = ok && l.fx && g.ny % s.rb == 0 && s.sa <= smem_cap && s.sb <= smem_cap;
+        c->has_fs = ok;
+    }
     return MM_OK;
 }
 
@@ -179,6 +210,7 @@ static void release(mm_ctx* c) {
         if (c->step_exec[p]) cudaGraphExecDestroy(c->step_exec[p]);
     cudaFree(c->Kt);
     cudaFree(c->S);
+    cudaFree(c->S2);
     cudaFree(c->Mbuf[0]);
     cudaFree(c->Mbuf[1]);
     cudaFree(c->H);
@@ -233,6 +265,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         const size_t N = (size_t)g.N;
         CU(cudaMalloc(&c->Kt, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.Hz));
         CU(cudaMalloc(&c->S, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
+        if (c->has_fs) CU(cudaMalloc(&c->S2, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
         CU(cudaMalloc(&c->Mbuf[0], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->Mbuf[1], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->H, sizeof(float) * 3 * N));
@@ -256,6 +289,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         g.twz = c->tw + g.Lx + g.Ly;
         g.Kt = c->Kt;
         CU(configure_pass_kernels(g, c->l));
+        if (c->has_fs) CU(configure_step_kernels(c->fs));
 
         // tensor set-up in FP64
         const int L[3] = {g.Lx, g.Ly, g.Lz};
@@ -326,6 +360,7 @@ extern "C" int mm_set_m(mm_ctx* c, const float* M) {
     if (!c || !M) return fail(MM_EINVAL, "null argument");
     CU(cudaMemcpyAsync(c->Mbuf[c->cur], M, sizeof(float) * 3 * (size_t)c->g.N, cudaMemcpyDefault, c->stream));
     CU(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    c->spec_valid = false;
     if (!is_device_ptr(M)) CU(cudaStreamSynchronize(c->stream));
     return MM_OK;
 }
@@ -337,8 +372,11 @@ extern "C" int mm_get_m(mm_ctx* c, float* M) {
     return MM_OK;
 }
 
+// The three-pass evaluation on the spectrum workspace S (which is also S[0]
+// of the two-kernel step, so it invalidates a pending spectrum).
 static int run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt, cudaStream_t s) {
     const LlgCoef cf = make_coef(c, dt);
+    c->spec_valid = false;
     CU(launch_pass1(c->g, c->l, M, c->S, s));
     CU(launch_plane(c->g, c->l, c->S, s));
     CU(launch_pass3(c->g, c->l, cf, mode, c->S, M, out, c->flag, s));
@@ -359,14 +397,28 @@ extern "C" int mm_effective_field(mm_ctx* c, const float* M, float* H) {
     return run_passes(c, kModeHeff, M, H, 0.0, c->stream);
 }
 
-// Capture one step (M[p] -> M[1-p]) on the private stream into a graph.
+static float2* spec(mm_ctx* c, int p) { return p == 0 ? c->S : c->S2; }
+
+// One step from parity p (M[p] -> M[1-p]).  Two-kernel path: K_A on S[p],
+// K_B into S[1-p], programmatic dependent launch between them.  Generic
+// path: the three passes on S.
+static int enqueue_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
+    if (c->has_fs) {
+        CU(launch_step_pdl(c->g, c->fs, make_coef(c, dt), spec(c, p), spec(c, 1 - p), c->Mbuf[p], c->Mbuf[1 - p],
+                           c->flag, s, true));
+        return MM_OK;
+    }
+    return run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, s);
+}
+
+// Capture one step from parity p on the private stream into a graph.
 static int capture_step(mm_ctx* c, int p, double dt) {
     if (c->step_exec[p]) {
         cudaGraphExecDestroy(c->step_exec[p]);
         c->step_exec[p] = nullptr;
     }
     CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    int rc = run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, c->cap);
+    int rc = enqueue_step(c, p, dt, c->cap);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
     if (rc != MM_OK) {
@@ -382,20 +434,31 @@ static int capture_step(mm_ctx* c, int p, double dt) {
     return MM_OK;
 }
 
+// Form S[cur] from M[cur] when the two-kernel step needs it.
+static int ensure_spectrum(mm_ctx* c) {
+    if (!c->has_fs || c->spec_valid) return MM_OK;
+    CU(launch_pass1(c->g, c->l, c->Mbuf[c->cur], spec(c, c->cur), c->stream));
+    c->spec_valid = true;
+    return MM_OK;
+}
+
 extern "C" int mm_step(mm_ctx* c, int n, double dt) {
     if (!c) return fail(MM_EINVAL, "null context");
     if (n < 0) return fail(MM_EINVAL, "n must be >= 0");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
+    if (n == 0) return MM_OK;
+    int rc = ensure_spectrum(c);
+    if (rc != MM_OK) return rc;
     for (int s = 0; s < n; ++s) {
         const int p = c->cur;
         if (c->use_graphs) {
             if (!c->step_exec[p] || c->step_dt[p] != dt || c->step_ver[p] != c->ver) {
-                int rc = capture_step(c, p, dt);
+                rc = capture_step(c, p, dt);
                 if (rc != MM_OK) return rc;
             }
             CU(cudaGraphLaunch(c->step_exec[p], c->stream));
         } else {
-            int rc = run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, c->stream);
+            rc = enqueue_step(c, p, dt, c->stream);
             if (rc != MM_OK) return rc;
         }
         c->cur = 1 - p;
@@ -440,7 +503,7 @@ extern "C" int mm_plan_info(const mm_ctx* c, int L[3]) {
         L[1] = c->g.Ly;
         L[2] = c->g.Lz;
     }
-    return 3;
+    return c->has_fs ? 2 : 3;
 }
 
 extern "C" int mm_tensor_octant(mm_ctx* c, double* out) {
@@ -478,11 +541,22 @@ extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsig
             const int p = c->cur;
             if (flush) CU(cudaMemsetAsync(flush, r & 0xff, (size_t)flush_bytes, c->stream));
             CU(cudaEventRecord(ev[0], c->stream));
-            CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
-            CU(cudaEventRecord(ev[1], c->stream));
-            CU(launch_plane(c->g, c->l, c->S, c->stream));
-            CU(cudaEventRecord(ev[2], c->stream));
-            CU(launch_pass3(c->g, c->l, cf, kModeStep, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag, c->stream));
+            if (c->has_fs) {
+                // pass 1 alone (the two-kernel step folds it into K_B), then K_A, K_B
+                CU(launch_pass1(c->g, c->l, c->Mbuf[p], spec(c, p), c->stream));
+                CU(cudaEventRecord(ev[1], c->stream));
+                CU(launch_step_a(c->g, c->fs, spec(c, p), c->stream, false));
+                CU(cudaEventRecord(ev[2], c->stream));
+                CU(launch_step_b(c->g, c->fs, cf, spec(c, p), spec(c, 1 - p), c->Mbuf[p], c->Mbuf[1 - p], c->flag,
+                                 c->stream, false));
+                c->spec_valid = true;
+            } else {
+                CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
+                CU(cudaEventRecord(ev[1], c->stream));
+                CU(launch_plane(c->g, c->l, c->S, c->stream));
+                CU(cudaEventRecord(ev[2], c->stream));
+                CU(launch_pass3(c->g, c->l, cf, kModeStep, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag, c->stream));
+            }
             CU(cudaEventRecord(ev[3], c->stream));
             CU(cudaEventSynchronize(ev[3]));
             for (int q = 0; q < 3; ++q) {

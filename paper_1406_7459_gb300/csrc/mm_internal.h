@@ -40,12 +40,16 @@ struct LlgCoef {
     float dt;
 };
 
+struct FastFns;
+
 // Launch shapes chosen at plan time.
 struct Launch {
     int r1, t1, g1;            // pass 1: rows per tile, threads, line group
     int t2, g2;                // pass 2 (plane): threads, line group
     int r3, t3, g3;            // pass 3: rows per tile, threads, line group
     size_t smem1, smem2, smem3;
+    const FastFns* fx = nullptr;     // compile-time x passes, if the grid has them
+    const FastFns* fp = nullptr;     // compile-time plane kernel, if available
 };
 
 enum Pass3Mode { kModeDemag = 0, kModeHeff = 1, kModeStep = 2 };
@@ -61,6 +65,44 @@ typedef void (*PlaneFn)(Geom, int, float2*);
 PlaneFn plane_fn_small(int Lz);   // plane_small.cu
 PlaneFn plane_fn_mid(int Lz);     // plane_mid.cu
 PlaneFn plane_fn_large(int Lz);   // plane_large.cu
+
+// Compile-time specialised kernels for power-of-two grids (fast_*.cu).
+struct FastFns {
+    void (*p1)(Geom, const float*, float2*) = nullptr;
+    int r1 = 0, t1 = 0;
+    size_t s1 = 0;
+    void (*pl)(Geom, float2*) = nullptr;
+    int t2 = 0;
+    size_t s2 = 0;
+    void (*p3[3])(Geom, LlgCoef, const float2*, const float*, float*, int*) = {nullptr, nullptr, nullptr};
+    int r3 = 0, t3 = 0;
+    size_t s3 = 0;
+};
+bool fast_lookup_x(int nx, FastFns* f);
+bool fast_lookup_plane_nz1(int ny, FastFns* f);
+bool fast_lookup_plane_nz2(int ny, FastFns* f);
+bool fast_lookup_plane_nz4(int ny, FastFns* f);
+bool fast_lookup_plane_nz8(int ny, FastFns* f);
+
+// Two-kernel step for power-of-two grids (fast_step*.cu): K_A = plane
+// kernel in place on S[p]; K_B = inverse x + LLG + forward x into S[1-p].
+struct FastStepFns {
+    void (*ka)(Geom, float2*) = nullptr;
+    int ta = 0;
+    size_t sa = 0;
+    void (*kb)(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*) = nullptr;
+    int rb = 0, tb = 0;
+    size_t sb = 0;
+};
+bool fast_step_lookup_x(int nx, FastStepFns* f);
+bool fast_step_lookup_plane_a(int ny, int nz, FastStepFns* f);
+bool fast_step_lookup_plane_b(int ny, int nz, FastStepFns* f);
+cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Snext,
+                            const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
+cudaError_t configure_step_kernels(const FastStepFns& f);
+cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, float2* S, cudaStream_t s, bool pdl);
+cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* S, float2* Snext,
+                          const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 
 // Tensor set-up (tensor_setup.cu).  Writes N (FP64 octant) and/or Kt.
 cudaError_t tensor_octant_fp64(const int grid[3], const double cell[3], double* N_dev, cudaStream_t s);

@@ -283,3 +283,71 @@ def test_argument_errors_on_gpu():
     with pytest.raises(_mm().MMError) as e:
         _mm().mm_create((8, 8, 9), cell, MS, A_EX, 0.0, 0.5, GAMMA)
     assert e.value.code == _mm().MM_EUNSUPPORTED
+
+
+POW2_GRIDS = [(16, 16, 1), (32, 32, 2), (64, 64, 4), (256, 256, 4), (128, 64, 8), (16, 1024, 1),
+              (1024, 16, 2), (512, 32, 1), (64, 512, 2), (32, 16, 8)]
+
+
+@pytest.mark.parametrize("nofast", ["0", "1"])
+@pytest.mark.parametrize("grid", POW2_GRIDS)
+def test_power_of_two_paths_demag_and_steps(grid, nofast, monkeypatch):
+    """The compile-time power-of-two kernels and the generic mixed-radix
+    kernels must both match the oracle on the grids the former cover."""
+    monkeypatch.setenv("MM_NO_FAST", nofast)
+    cell = (4e-9, 4e-9, 3e-9)
+    Ku, alpha, dt, Hext = 1e4, 0.1, 5e-14, (1e4, -5e3, 2e3)
+    M = inputs.random_unit_m(grid, MS, seed=31)
+    ctx = _ctx(grid, cell, Ku=Ku, alpha=alpha)
+    Md = _dev(M)
+    Hd = torch.empty_like(Md)
+    _mm().mm_demag_field(ctx, Md, Hd)
+    Kt, Lp = oracle_spectrum(grid, cell)
+    M64 = M.astype(np.float64)
+    Href = D.demag_fft(M64, Kt, Lp)
+    assert rel_l2(_host(Hd, grid), Href) < 1e-5
+    assert rel_max(_host(Hd, grid), Href) < 1e-5
+    _mm().mm_set_field(ctx, Hext)
+    _mm().mm_set_m(ctx, Md)
+    _mm().mm_step(ctx, 3, dt)
+    out = torch.empty_like(Md)
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    ref = L.run_euler(M64, 3, dt, cell, MS, A_EX, Ku, alpha, GAMMA, Hext, Kt, Lp)
+    assert rel_l2(_host(out, grid), ref) < 1e-5
+
+
+@pytest.mark.parametrize("grid", [(64, 32, 4), (48, 20, 3)])
+def test_steps_interleaved_with_other_calls(grid):
+    """Steps, field evaluations, energies and state changes in any order give
+    the same trajectory as the oracle (the two-kernel step keeps the next
+    step's spectrum between calls and must notice when it is stale)."""
+    cell = (4e-9, 4e-9, 3e-9)
+    Ku, alpha, dt, Hext = 2e4, 0.2, 5e-14, (2e4, 1e4, -3e3)
+    M = inputs.random_unit_m(grid, MS, seed=41)
+    M2 = inputs.random_unit_m(grid, MS, seed=42)
+    ctx = _ctx(grid, cell, Ku=Ku, alpha=alpha)
+    _mm().mm_set_field(ctx, Hext)
+    _mm().mm_set_m(ctx, _dev(M))
+    Kt, Lp = oracle_spectrum(grid, cell)
+    ref = M.astype(np.float64)
+    args = (dt, cell, MS, A_EX, Ku, alpha, GAMMA, Hext, Kt, Lp)
+    scratch_in = _dev(M2)
+    scratch_out = torch.empty_like(scratch_in)
+    for n, action in ((3, "demag"), (2, "energy"), (1, "heff"), (4, "setm"), (2, None)):
+        _mm().mm_step(ctx, n, dt)
+        ref = L.run_euler(ref, n, *args)
+        if action == "demag":
+            _mm().mm_demag_field(ctx, scratch_in, scratch_out)
+        elif action == "energy":
+            _mm().mm_energy(ctx)
+        elif action == "heff":
+            _mm().mm_effective_field(ctx, scratch_in, scratch_out)
+        elif action == "setm":
+            _mm().mm_set_m(ctx, scratch_in)
+            ref = M2.astype(np.float64)
+    out = torch.empty_like(scratch_in)
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    assert rel_l2(_host(out, grid) - M2, ref - M2) < 1e-4
+    assert rel_l2(_host(out, grid), ref) < 1e-6
