@@ -180,6 +180,40 @@ int mm_kernel_spectrum(mm_ctx *ctx, float *out);
 int mm_time_passes(mm_ctx *ctx, int reps, double dt, void *flush, unsigned long long flush_bytes,
                    float ms[3]);
 
+/*
+ * mm_demag_field_noalloc -- H_demag of M, like mm_demag_field, for callers
+ * that cannot allocate device memory: for example a host program that
+ * reserves its whole device-memory budget up front and forbids later
+ * allocation, or code on a latency-critical path where cudaMalloc (which may
+ * synchronise the device) is not allowed.  No context is needed and nothing
+ * is allocated (no cudaMalloc, cudaFree or allocating library routine): the
+ * only workspace is one file-scope device array of 8 MiB inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The paper has no counterpart; it is an interface addition.
+ *
+ *   grid      {nx, ny, nz}, the same limits as mm_create; the twiddle tables
+ *             plus the x half-spectrum workspace, (Lx+Ly+Lz) + 3*(Lx/2+1)*ny*nz
+ *             complex floats (each padded length chosen as in mm_create), must
+ *             fit in the 8 MiB array (e.g. 256 x 256 x 4 fits, 512 x 512 x 8
+ *             does not); larger grids return MM_EUNSUPPORTED with the sizes
+ *             in mm_last_error().
+ *   Kt_dev    the scaled tensor spectrum exactly as mm_kernel_spectrum
+ *             copies it out of a context built for the same grid and cell
+ *             (device memory).
+ *   M_dev, H_dev  3*N float32 device arrays, must not overlap.
+ *   cuda_stream   stream to run on (NULL = legacy default stream).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and its last
+ * contents: calls whose GPU work overlaps in time (other streams, other host
+ * threads) race and give wrong results, so serialise them.  Each call writes
+ * every workspace element it reads before reading it, so no clearing is
+ * needed.  Asynchronous.  Returns MM_EINVAL, MM_EUNSUPPORTED or MM_ECUDA.
+ */
+int mm_demag_field_noalloc(const int grid[3], const float *Kt_dev, const float *M_dev, float *H_dev,
+                           void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

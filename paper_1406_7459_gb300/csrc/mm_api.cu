@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/mm.h"
@@ -571,5 +572,82 @@ extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsig
     for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
     if (rc != MM_OK) return rc;
     for (int q = 0; q < 3; ++q) ms[q] = (float)(acc[q] / reps);
+    return MM_OK;
+}
+
+// ----------------------------------------------------- no-allocation entry --
+// Callers that may not allocate device memory (a host that runs with a fixed
+// memory budget, code that executes where cudaMalloc is forbidden or would
+// synchronise the device) evaluate the demag field through
+// mm_demag_field_noalloc.  Its only workspace is this file-scope device
+// array: every GPU that loads the library holds it until the process exits.
+// Layout per call: twiddles W_Lx, W_Ly, W_Lz, then the spectrum workspace.
+static constexpr size_t kNoAllocComplex = (size_t)1 << 20;    // 8 MiB of float2
+static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocComplex];
+
+static std::mutex g_noalloc_mu;
+static float2* g_noalloc_ptr[64] = {nullptr};     // device address per device ordinal
+
+__global__ void k_noalloc_twiddles(int Lx, int Ly, int Lz, float2* tw) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    int L, e;
+    if (m < Lx) { L = Lx; e = m; }
+    else if (m < Lx + Ly) { L = Ly; e = m - Lx; }
+    else if (m < Lx + Ly + Lz) { L = Lz; e = m - Lx - Ly; }
+    else return;
+    double s, c;
+    sincospi(-2.0 * e / L, &s, &c);
+    tw[m] = make_float2((float)c, (float)s);
+}
+
+extern "C" int mm_demag_field_noalloc(const int grid[3], const float* Kt_dev, const float* M_dev, float* H_dev,
+                                      void* cuda_stream) {
+    if (!grid || !Kt_dev || !M_dev || !H_dev) return fail(MM_EINVAL, "null argument");
+    for (int a = 0; a < 3; ++a)
+        if (grid[a] < 1) return fail(MM_EINVAL, "grid[%d] = %d < 1", a, grid[a]);
+    if ((long long)grid[0] * grid[1] * grid[2] > (1LL << 28)) return fail(MM_EUNSUPPORTED, "grid too large");
+    // plan on a stack context: no device or host allocation
+    mm_ctx tmp;
+    for (int a = 0; a < 3; ++a) tmp.grid[a] = grid[a];
+    int rc = build_plan(&tmp);
+    if (rc != MM_OK) return rc;
+    Geom g = tmp.g;
+    const size_t N = (size_t)g.N;
+    if (overlap(M_dev, H_dev, 3 * N)) return fail(MM_EINVAL, "M and H overlap");
+    const size_t ntw = (size_t)g.Lx + g.Ly + g.Lz;
+    const size_t nspec = (size_t)g.Hx * 3 * g.nz * g.Jst;
+    const size_t need = ((ntw + 31) & ~(size_t)31) + nspec;
+    if (need > kNoAllocComplex)
+        return fail(MM_EUNSUPPORTED,
+                    "grid %dx%dx%d needs %zu bytes of workspace; the static workspace holds %zu bytes",
+                    grid[0], grid[1], grid[2], need * sizeof(float2), kNoAllocComplex * sizeof(float2));
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(MM_EUNSUPPORTED, "device ordinal %d out of range", dev);
+    float2* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = (float2*)p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float2* tw = base;
+    float2* S = base + ((ntw + 31) & ~(size_t)31);
+    g.twx = tw;
+    g.twy = tw + g.Lx;
+    g.twz = tw + g.Lx + g.Ly;
+    g.Kt = Kt_dev;
+    CU(configure_pass_kernels(g, tmp.l));
+    k_noalloc_twiddles<<<(unsigned)((ntw + 255) / 256), 256, 0, s>>>(g.Lx, g.Ly, g.Lz, tw);
+    CU(cudaGetLastError());
+    // every workspace element the passes read is written earlier in this call
+    const LlgCoef cf{};
+    CU(launch_pass1(g, tmp.l, M_dev, S, s));
+    CU(launch_plane(g, tmp.l, S, s));
+    CU(launch_pass3(g, tmp.l, cf, kModeDemag, S, M_dev, H_dev, nullptr, s));
     return MM_OK;
 }

@@ -42,6 +42,7 @@ _PROTOS = {
     "mm_kernel_spectrum": (_c_int, [_vp, _vp]),
     "mm_time_passes": (_c_int, [_vp, _c_int, _c_double, _vp, ctypes.c_ulonglong,
                                 ctypes.POINTER(ctypes.c_float)]),
+    "mm_demag_field_noalloc": (_c_int, [ctypes.POINTER(_c_int), _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -183,10 +184,14 @@ def mm_tensor_octant(ctx):
     return out
 
 
-def mm_kernel_spectrum(ctx):
+def mm_kernel_spectrum(ctx, out=None):
+    """Copy of the stored tensor spectrum; into `out` (torch or numpy,
+    float32, (Lx/2+1)*(Lz/2+1)*(Ly/2+1)*6 elements) when given."""
     (Lx, Ly, Lz), _ = mm_plan_info(ctx)
-    out = np.zeros((Lx // 2 + 1, Lz // 2 + 1, Ly // 2 + 1, 6), np.float32)
-    _check(lib().mm_kernel_spectrum(ctx.handle, _vp(_ptr(out))))
+    n = (Lx // 2 + 1) * (Lz // 2 + 1) * (Ly // 2 + 1) * 6
+    if out is None:
+        out = np.zeros((Lx // 2 + 1, Lz // 2 + 1, Ly // 2 + 1, 6), np.float32)
+    _check(lib().mm_kernel_spectrum(ctx.handle, _vp(_ptr(out, n))))
     return out
 
 
@@ -198,3 +203,13 @@ def mm_time_passes(ctx, reps, dt, flush=None):
     fbytes = flush.numel() * flush.element_size() if flush is not None else 0
     _check(lib().mm_time_passes(ctx.handle, int(reps), float(dt), _vp(fptr), fbytes, ms))
     return tuple(ms)
+
+
+def mm_demag_field_noalloc(grid, Kt, M, H, stream=None):
+    """Demag field without any device allocation (see include/mm.h): Kt is
+    the device copy of mm_kernel_spectrum for the same grid and cell."""
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    n = 3 * int(grid[0]) * int(grid[1]) * int(grid[2])
+    _check(lib().mm_demag_field_noalloc(g, _vp(_ptr(Kt)), _vp(_ptr(M, n)), _vp(_ptr(H, n)),
+                                        _vp(_stream_handle(stream))))
+    return H
