@@ -54,16 +54,25 @@ def config_dict():
 
 
 def algorithmic_bytes(grid):
-    """Bytes each pass must move at least once (FP32 SoA M, complex64
-    half-spectrum X = (Lx/2+1)*ny*nz per component, FP32 tensor octant
-    Ks = (Lx/2+1)(Ly/2+1)(Lz/2+1) bins x 6)."""
+    """Bytes each kernel must move at least once, FP32 SoA M (12 B/cell),
+    complex64 x half-spectrum X = (Lx/2+1)*ny*nz per component (24 B per
+    X element for three components).
+    Three-pass model (the generic path and the reference accounting):
+      pass 1 12N + 24X, plane 48X + 24Ks, pass 3 24X + 24N,
+      Ks = (Lx/2+1)(Ly/2+1)(Lz/2+1) octant bins x 6 floats.
+    Two-kernel power-of-two step (this benchmark):
+      K_A plane 48X + 24Kd, K_B x-step 48X + 24N,
+      Kd = (Lx/2+1)(Ly/2+1) nz coupling sets x 6 floats."""
     nx, ny, nz = grid
     L = [1 if n == 1 else 2 * n for n in grid]     # power-of-two grids here
     N = nx * ny * nz
     X = (L[0] // 2 + 1) * ny * nz
     Ks = (L[0] // 2 + 1) * (L[1] // 2 + 1) * (L[2] // 2 + 1)
-    return {"pass1": 12 * N + 24 * X, "pass2": 48 * X + 24 * Ks, "pass3": 24 * X + 24 * N,
-            "step": 36 * N + 96 * X + 24 * Ks, "demag": 24 * N + 96 * X + 24 * Ks}
+    Kd = (L[0] // 2 + 1) * (L[1] // 2 + 1) * nz
+    return {"pass1": 12 * N + 24 * X, "plane3": 48 * X + 24 * Ks, "pass3": 24 * X + 24 * N,
+            "step3": 36 * N + 96 * X + 24 * Ks,
+            "kA": 48 * X + 24 * Kd, "kB": 48 * X + 24 * N, "step2": 24 * N + 96 * X + 24 * Kd,
+            "demag": 24 * N + 96 * X + 24 * Ks}
 
 
 def measured_peaks():
@@ -231,7 +240,8 @@ def run_gpu(args, rank, ws):
     t_local = sum(step_ms) / 1e3
     mm.mm_sync(ctx)
 
-    # --- per-pass durations (same cold-L2 protocol), for the roofline
+    # --- per-kernel durations (same cold-L2 protocol, kernels launched one
+    # by one without programmatic overlap), for the roofline
     reps = min(K, 200)
     p1, p2, p3 = mm.mm_time_passes(ctx, reps, dt, flush)
 
@@ -277,10 +287,18 @@ def run_gpu(args, rank, ws):
     value = ws * N * K / t_max
     by = algorithmic_bytes(GRID)
     peak, peak_kind = measured_peaks()
-    passes = {"pass1_x_r2c": p1, "pass2_yz_plane": p2, "pass3_x_c2r_llg": p3}
-    dom = max(passes, key=passes.get)
-    dom_bytes = {"pass1_x_r2c": by["pass1"], "pass2_yz_plane": by["pass2"], "pass3_x_c2r_llg": by["pass3"]}[dom]
-    achieved = dom_bytes / (passes[dom] * 1e-3) / 1e9
+    _, launches = mm.mm_plan_info(ctx)
+    if launches == 2:
+        passes = {"pass1_x_r2c_first_step_only": p1, "kA_plane_y_zsum_product": p2,
+                  "kB_x_c2r_llg_euler_x_r2c": p3}
+        kbytes = {"kA_plane_y_zsum_product": by["kA"], "kB_x_c2r_llg_euler_x_r2c": by["kB"]}
+        step_bytes = by["step2"]
+    else:
+        passes = {"pass1_x_r2c": p1, "pass2_yz_plane": p2, "pass3_x_c2r_llg": p3}
+        kbytes = {"pass1_x_r2c": by["pass1"], "pass2_yz_plane": by["plane3"], "pass3_x_c2r_llg": by["pass3"]}
+        step_bytes = by["step3"]
+    dom = max(kbytes, key=lambda k: passes[k])
+    achieved = kbytes[dom] / (passes[dom] * 1e-3) / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
@@ -294,13 +312,18 @@ def run_gpu(args, rank, ws):
         "ms_per_step": step_ms_mean, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic", "config": config_dict(),
         "demag_evals_per_s": ws * 1e3 / demag_ms,
-        "step_hbm": {"algorithmic_bytes": by["step"], "gbs": by["step"] / (step_ms_mean * 1e-3) / 1e9,
-                     "frac": by["step"] / (step_ms_mean * 1e-3) / 1e9 / peak},
+        "step_hbm": {"algorithmic_bytes": step_bytes, "model": "two-kernel" if launches == 2 else "three-pass",
+                     "gbs": step_bytes / (step_ms_mean * 1e-3) / 1e9,
+                     "frac": step_bytes / (step_ms_mean * 1e-3) / 1e9 / peak,
+                     "three_pass_model_bytes": by["step3"],
+                     "three_pass_model_frac": by["step3"] / (step_ms_mean * 1e-3) / 1e9 / peak},
         "pass_ms": passes,
+        "launches_per_step": launches,
         "steady_state_l2_resident": {"ms_per_step": warm_ms, "cells_steps_per_s": ws * N / (warm_ms * 1e-3)},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic},
-        "gpu_launches": 3 * K,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": kbytes[dom]},
+        "gpu_launches": launches * K,
         "clocks": clocks,
         "e2e": {"value": ws * N * ke / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N},

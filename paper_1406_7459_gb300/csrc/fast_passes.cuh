@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(R * Fft2<N>::G) k_pass1_fast(Geom g, const flo
         for (int q = 0; q < P; ++q) {
             const int j = t + Q * q;
             v[q] = make_float2(__ldg(ra + j), __ldg(rb + j));
-            if (h) v[q] = cmul(v[q], tw[j]);
         }
+        if (h) F::odd_input(v, t, tw);
         F::stepA(v, t, tw, ex + grp * F::EX, false);
     }
     __syncthreads();
@@ -177,8 +177,8 @@ __global__ void __launch_bounds__(6 * NZ * Fft2<NY>::G, (6 * NZ * Fft2<NY>::G <=
         for (int q = 0; q < P; ++q) {
             const int j = t + Q * q;
             v[q] = src[j];
-            if (h) v[q] = cmul(v[q], tw[j]);
         }
+        if (h) F::odd_input(v, t, tw);
         F::stepA(v, t, tw, ex + grp * F::EX, false);
     }
     __syncthreads();

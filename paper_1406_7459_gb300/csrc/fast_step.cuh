@@ -1,8 +1,11 @@
 // fast_step.cuh -- the two-kernel Euler step for power-of-two grids.
 //
 // Step n (spectrum S[p] of M^n already formed):
-//   K_A  k_plane_pdl   per kx plane: y FFT, z DFT, tensor product (Eq. (15)),
-//                      inverse z, inverse y, in place on S[p].
+//   K_A  k_plane_pdl   per kx plane: y FFT, the z part of the convolution
+//                      as a direct sum over the nz layers with the (x, y)
+//                      tensor spectrum of each z offset (exact, and cheaper
+//                      than a length-2nz transform pair for nz <= 8), the
+//                      tensor product (Eq. (15)), inverse y; in place on S[p].
 //   K_B  k_xstep_pdl   per (layer, row pair): inverse x C2R (Eq. (16)), the
 //                      field and LLG update of Eqs. (2)-(6) with the Euler
 //                      step and renormalisation, and then the forward x R2C
@@ -35,16 +38,60 @@ template <int a, int b> struct cmax { static constexpr int v = a > b ? a : b; };
 // ------------------------------------------------------------- K_A plane --
 template <int NY, int NZ> struct PlaneLayout {
     using F = Fft2<NY>;
-    static constexpr int LY = 2 * NY, ZS = pzlen(2 * NY), NL = 3 * NZ;
-    static constexpr int HZ = (NZ == 1) ? 1 : NZ + 1;   // Lz/2 + 1
+    static constexpr int LY = 2 * NY, NL = 3 * NZ;
+    static constexpr int ZS = 2 * NY + 2;                 // line stride: [h][m], two halves of NY
     static constexpr int HY = NY + 1;
-    static constexpr int KT_FLOATS = HZ * HY * 6;
+    static constexpr int KT_FLOATS = HY * NZ * 6;         // one kx slice of the 2-D spectrum
+    // held in shared memory transposed, [dz*6 + c][ky], so that consecutive
+    // threads (consecutive ky) read consecutive words
     static constexpr int KT_C = (KT_FLOATS + 1) / 2;      // in float2 units
     static constexpr int WORK = cmax<NL * ZS, 2 * NL * F::EX>::v;
     static constexpr int TW_OFF = 0, KT_OFF = LY, WORK_OFF = LY + ((KT_C + 1) / 2) * 2;
     static constexpr size_t BYTES = sizeof(float2) * (WORK_OFF + WORK);
     static constexpr int THREADS = 2 * NL * F::G;
+    static constexpr int ZTASKS = 3 * LY;                 // (ky column, output component)
+    static constexpr int ZTPT = (ZTASKS + THREADS - 1) / THREADS;
 };
+
+// Direct z sum of one (kx, ky) column for output component a, with
+// M_z' = i M_z and H_z' = i H_z (real couplings, see k_pack2d):
+//   H'_a(k) = sum_k' sum_b D_ab(k - k') M'_b(k'),
+// D(dz) from the stored d(|dz|) = (xx, xy, xz, yy, yz, zz): row x uses
+// (xx, xy, xz), row y (xy, yy, yz), row z' (-xz, -yz, zz); xz and yz change
+// sign for dz < 0 (odd in z) and xy, yz for a mirrored ky (odd in y).
+template <int NZ, int HY>
+__device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], const float* __restrict__ d, int a, float sy,
+                                             float2 (&h)[NZ]) {
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) h[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int dz = 0; dz < NZ; ++dz) {
+        const float xx = d[(dz * 6 + 0) * HY], xy = sy * d[(dz * 6 + 1) * HY], xz = d[(dz * 6 + 2) * HY];
+        const float yy = d[(dz * 6 + 3) * HY], yz = sy * d[(dz * 6 + 4) * HY], zz = d[(dz * 6 + 5) * HY];
+        float cb0, cb1, cb2;                              // D_a,b for b = x, y, z' at +dz
+        float ob0, ob1, ob2;                              // sign-adjusted for -dz
+        if (a == 0) { cb0 = xx; cb1 = xy; cb2 = xz; ob0 = xx; ob1 = xy; ob2 = -xz; }
+        else if (a == 1) { cb0 = xy; cb1 = yy; cb2 = yz; ob0 = xy; ob1 = yy; ob2 = -yz; }
+        else { cb0 = -xz; cb1 = -yz; cb2 = zz; ob0 = xz; ob1 = yz; ob2 = zz; }
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) {
+            // k - k' = +dz  -> k' = k - dz
+            if (k - dz >= 0) {
+                const int kp = k - dz;
+                h[k] = cfma_real(cb0, m[0][kp], h[k]);
+                h[k] = cfma_real(cb1, m[1][kp], h[k]);
+                h[k] = cfma_real(cb2, m[2][kp], h[k]);
+            }
+            // k - k' = -dz (dz > 0) -> k' = k + dz
+            if (dz > 0 && k + dz < NZ) {
+                const int kp = k + dz;
+                h[k] = cfma_real(ob0, m[0][kp], h[k]);
+                h[k] = cfma_real(ob1, m[1][kp], h[k]);
+                h[k] = cfma_real(ob2, m[2][kp], h[k]);
+            }
+        }
+    }
+}
 
 template <int NY, int NZ>
 __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY, NZ>::THREADS <= 512) ? 2 : 1)
@@ -61,10 +108,17 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
 
     // prologue: constant data only
     for (int i = threadIdx.x; i < LY / 2; i += blockDim.x) copy16(tw + 2 * i, g.twy + 2 * i);
-    const float* Kp = g.Kt + (size_t)kx * Lay::KT_FLOATS;
-    // the slice starts 8-byte aligned; copy it as float2 pairs through registers
-    for (int i = threadIdx.x; i < Lay::KT_FLOATS / 2; i += blockDim.x)
-        reinterpret_cast<float2*>(Ks)[i] = __ldg(reinterpret_cast<const float2*>(Kp) + i);
+    const float* Kp = g.Kd + (size_t)kx * Lay::KT_FLOATS;
+    // copy the slice through registers, transposing [ky][dz*6 + c] -> [dz*6 + c][ky]
+    for (int ky = threadIdx.x; ky < Lay::HY; ky += blockDim.x) {
+        const float2* src = reinterpret_cast<const float2*>(Kp + (size_t)ky * NZ * 6);
+#pragma unroll
+        for (int q = 0; q < NZ * 3; ++q) {
+            const float2 v2 = __ldg(src + q);
+            Ks[(2 * q) * Lay::HY + ky] = v2.x;
+            Ks[(2 * q + 1) * Lay::HY + ky] = v2.y;
+        }
+    }
     __pipeline_commit();
     pdl_wait();
 
@@ -81,10 +135,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     __syncthreads();
     // forward y (pruned input): odd half pre-multiplied by W_LY^j
     if (t < Q) {
-        if (h) {
-#pragma unroll
-            for (int q = 0; q < P; ++q) v[q] = cmul(v[q], tw[t + Q * q]);
-        }
+        if (h) F::odd_input(v, t, tw);
         F::stepA(v, t, tw, ex + grp * F::EX, false);
     }
     __syncthreads();
@@ -93,46 +144,68 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     __syncthreads();
     if (t < P) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) zb[line * ZS + pz(2 * (t + P * q) + h)] = w[q];
+        for (int q = 0; q < Q; ++q) zb[line * ZS + h * NY + t + P * q] = w[q];
     }
     __syncthreads();
-    for (int ky = threadIdx.x; ky < LY; ky += blockDim.x) {
+    // z part of the convolution: direct sum over the layers, one (ky)
+    // column per task, read and written back by the same thread
+    for (int col = threadIdx.x; col < LY; col += blockDim.x) {
+        const int hh = col / NY, mm = col - hh * NY;      // ky = 2 mm + hh
+        const int ky = 2 * mm + hh;
+        const int e = hh * NY + mm;
         float2 m[3][NZ];
-        const int e = pz(ky);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int k = 0; k < NZ; ++k) m[c][k] = zb[(c * NZ + k) * ZS + e];
-        zconv_column<NZ>(m, Ks, Lay::HY, LY, ky, g.twz);
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < NZ; ++k) m[2][k] = make_float2(-m[2][k].y, m[2][k].x);   // i M_z
+        int kyp = ky;
+        float sy = 1.f;
+        if (2 * ky > LY) { kyp = LY - ky; sy = -1.f; }
+        float2 hres[NZ];
 #pragma unroll
-            for (int k = 0; k < NZ; ++k) zb[(c * NZ + k) * ZS + e] = m[c][k];
+        for (int a = 0; a < 3; ++a) {
+            zdirect_task<NZ, Lay::HY>(m, Ks + kyp, a, sy, hres);
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) {
+                const float2 o = (a == 2) ? make_float2(hres[k].y, -hres[k].x) : hres[k];   // -i H_z'
+                zb[(a * NZ + k) * ZS + e] = o;
+            }
+        }
     }
     __syncthreads();
     // inverse y (pruned output)
     if (t < Q) {
 #pragma unroll
-        for (int q = 0; q < P; ++q) v[q] = zb[line * ZS + pz(2 * (t + Q * q) + h)];
+        for (int q = 0; q < P; ++q) v[q] = zb[line * ZS + h * NY + t + Q * q];
     }
     __syncthreads();
     if (t < Q) F::stepA(v, t, tw, ex + grp * F::EX, true);
     __syncthreads();
-    if (t < P) F::stepB(w, t, ex + grp * F::EX, true);
-    __syncthreads();
     if (t < P) {
+        F::stepB(w, t, ex + grp * F::EX, true);
+        if (h) F::odd_output(w, t, tw);
+    }
+    if constexpr (G == 16) {
+        // the two halves of a line are lanes t and t + 16 of one warp
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int n = t + P * q;
-            float2 val = w[q];
-            if (h) val = cmul(val, cconj(tw[n]));
-            zb[line * ZS + pz(h * NY + n)] = val;
+            const float ox = __shfl_down_sync(0xffffffffu, w[q].x, 16);
+            const float oy = __shfl_down_sync(0xffffffffu, w[q].y, 16);
+            if (h == 0) plane[(size_t)line * g.Jst + t + P * q] = make_float2(w[q].x + ox, w[q].y + oy);
         }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
-        const int l = idx / NY, n = idx % NY;
-        plane[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + pz(n)], zb[l * ZS + pz(NY + n)]);
+    } else {
+        __syncthreads();
+        if (t < P) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) zb[line * ZS + h * NY + t + P * q] = w[q];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
+            const int l = idx / NY, n = idx % NY;
+            plane[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + NY + n]);
+        }
     }
     __syncthreads();
     pdl_trigger();
@@ -141,7 +214,9 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
 // ------------------------------------------------------------- K_B xstep --
 template <int N, int R> struct XstepLayout {
     using F = Fft2<N>;
-    static constexpr int L = 2 * N, H = N + 1, NL = 3 * R / 2, ZS = pzlen(2 * N);
+    static constexpr int L = 2 * N, H = N + 1, NL = 3 * R / 2;
+    static constexpr int ZS = 2 * N + 2;                  // forward line stride: [h][m] halves of N
+    static constexpr int HM = N / 2 + 1;                  // staged kx per parity: kx = 2 m + parity
     static constexpr int MROWS = 3 * R + 2;                // rows of the M tile per component
     static constexpr int TW_OFF = 0;
     static constexpr int MT_OFF = L;                              // float2 units; floats: 3*MROWS*N
@@ -203,15 +278,14 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     }
     __pipeline_commit();
     pdl_wait();
-    // staged half-spectrum of the H tile: sb[(c*H + kx)*R + r]
-    {
-        constexpr int RC = R / 2;                               // 16-byte chunks per (kx, c)
-        for (int idx = threadIdx.x; idx < 3 * H * RC; idx += blockDim.x) {
-            const int q = idx % RC;
-            const int rest = idx / RC;
-            const int kx = rest % H, c = rest / H;
-            copy16(sb + (size_t)(c * H + kx) * R + 2 * q,
-                   S + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * q);
+    // staged half-spectrum of the H tile: sb[(c*H + kx)*R + r] (R = 2:
+    // one 16-byte copy per (kx, c))
+    for (int kx = threadIdx.x; kx < H; kx += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2* src = S + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0;
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) copy16(sb + (size_t)(c * H + kx) * R + 2 * q, src + 2 * q);
         }
     }
     __pipeline_commit();
@@ -239,15 +313,29 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         F::stepA(v, t, tw, wk + grp * F::EX, true);
     }
     __syncthreads();
-    if (fft_thread && t < P) F::stepB(w, t, wk + grp * F::EX, true);
-    __syncthreads();
     if (fft_thread && t < P) {
+        F::stepB(w, t, wk + grp * F::EX, true);
+        if (h) F::odd_output(w, t, tw);
+    }
+    __syncthreads();
+    if constexpr (G == 16) {
+        // halves of a line sit in lanes t and t + 16 of one warp: combine
+        // by shuffle and keep only the sum, ob[line][n]
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int n = t + P * q;
-            float2 val = w[q];
-            if (h) val = cmul(val, cconj(tw[n]));
-            wk[line * L + h * N + n] = val;                     // ob[line][h][n]
+            const float ox = __shfl_down_sync(0xffffffffu, w[q].x, 16);
+            const float oy = __shfl_down_sync(0xffffffffu, w[q].y, 16);
+            if (fft_thread && h == 0) wk[line * L + t + P * q] = make_float2(w[q].x + ox, w[q].y + oy);
+        }
+    } else {
+        if (fft_thread && t < P) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) wk[line * L + h * N + t + P * q] = w[q];   // ob[line][h][n]
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < NL * N; idx += blockDim.x) {
+            const int ln = idx / N, n = idx % N;
+            wk[ln * L + n] = cadd(wk[ln * L + n], wk[ln * L + N + n]);
         }
     }
     __syncthreads();
@@ -260,7 +348,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
             const int ln = cc * (R / 2) + (r >> 1);
-            const float2 z = cadd(wk[ln * L + i], wk[ln * L + N + i]);
+            const float2 z = wk[ln * L + i];
             hd[cc] = (r & 1) ? z.y : z.x;
         }
         const int im = i > 0 ? i - 1 : i, ip = i + 1 < N ? i + 1 : i;
@@ -309,8 +397,8 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         for (int q = 0; q < P; ++q) {
             const int jx = t + Q * q;
             v[q] = make_float2(ra[jx], rb[jx]);
-            if (h) v[q] = cmul(v[q], tw[jx]);
         }
+        if (h) F::odd_input(v, t, tw);
         F::stepA(v, t, tw, wk + grp * F::EX, false);
     }
     __syncthreads();
@@ -318,7 +406,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     __syncthreads();
     if (fft_thread && t < P) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) wk[line * ZS + pz(2 * (t + P * q) + h)] = w[q];
+        for (int q = 0; q < Q; ++q) wk[line * ZS + h * N + t + P * q] = w[q];
     }
     __syncthreads();
     // split each pair into the two rows' half-spectra and store to Snext
@@ -327,8 +415,9 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         const int rest = idx / (R / 2);
         const int c = rest % 3, kx = rest / 3;
         const float2* ln = wk + (c * (R / 2) + q) * ZS;
-        const float2 zk = ln[pz(kx)];
-        const float2 zm = ln[pz((L - kx) & (L - 1))];
+        const int km = (L - kx) & (L - 1);
+        const float2 zk = ln[(kx & 1) * N + (kx >> 1)];
+        const float2 zm = ln[(km & 1) * N + (km >> 1)];
         const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
                                      0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
         *reinterpret_cast<float4*>(Snext + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * q) = o;

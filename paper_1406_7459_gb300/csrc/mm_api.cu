@@ -45,6 +45,7 @@ struct mm_ctx {
     Geom g;
     Launch l;
     float* Kt = nullptr;
+    float* Kd = nullptr;       // 2-D spectrum per z offset (two-kernel step only)
     float2* S = nullptr;
     float* Mbuf[2] = {nullptr, nullptr};
     int cur = 0;
@@ -210,6 +211,7 @@ static void release(mm_ctx* c) {
     for (int p = 0; p < 2; ++p)
         if (c->step_exec[p]) cudaGraphExecDestroy(c->step_exec[p]);
     cudaFree(c->Kt);
+    cudaFree(c->Kd);
     cudaFree(c->S);
     cudaFree(c->S2);
     cudaFree(c->Mbuf[0]);
@@ -266,7 +268,10 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         const size_t N = (size_t)g.N;
         CU(cudaMalloc(&c->Kt, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.Hz));
         CU(cudaMalloc(&c->S, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
-        if (c->has_fs) CU(cudaMalloc(&c->S2, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
+        if (c->has_fs) {
+            CU(cudaMalloc(&c->S2, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
+            CU(cudaMalloc(&c->Kd, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.nz));
+        }
         CU(cudaMalloc(&c->Mbuf[0], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->Mbuf[1], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->H, sizeof(float) * 3 * N));
@@ -289,6 +294,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         g.twy = c->tw + g.Lx;
         g.twz = c->tw + g.Lx + g.Ly;
         g.Kt = c->Kt;
+        g.Kd = c->Kd;
         CU(configure_pass_kernels(g, c->l));
         if (c->has_fs) CU(configure_step_kernels(c->fs));
 
@@ -300,7 +306,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         if (e == cudaSuccess) e = cudaMalloc(&w1, sizeof(double) * wn);
         if (e == cudaSuccess) e = cudaMalloc(&w2, sizeof(double) * wn);
         if (e == cudaSuccess) e = tensor_octant_fp64(c->grid, c->cell, Nd, c->stream);
-        if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream);
+        if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream, c->Kd);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         cudaFree(Nd);
         cudaFree(w1);
@@ -641,6 +647,7 @@ extern "C" int mm_demag_field_noalloc(const int grid[3], const float* Kt_dev, co
     g.twy = tw + g.Lx;
     g.twz = tw + g.Lx + g.Ly;
     g.Kt = Kt_dev;
+    g.Kd = nullptr;
     CU(configure_pass_kernels(g, tmp.l));
     k_noalloc_twiddles<<<(unsigned)((ntw + 255) / 256), 256, 0, s>>>(g.Lx, g.Ly, g.Lz, tw);
     CU(cudaGetLastError());

@@ -26,6 +26,8 @@ struct Geom {
     const float2* twy;
     const float2* twz;
     const float* Kt;           // tensor spectrum [kx][kz'][ky'][6], scaled
+    const float* Kd;           // 2-D (x, y) tensor spectrum per z offset [kx][ky'][dz][6], scaled;
+                               // used by the direct-z plane kernel of the power-of-two step
 };
 
 // Field and LLG coefficients in FP32 (computed in FP64 on the host).
@@ -107,7 +109,7 @@ cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c,
 // Tensor set-up (tensor_setup.cu).  Writes N (FP64 octant) and/or Kt.
 cudaError_t tensor_octant_fp64(const int grid[3], const double cell[3], double* N_dev, cudaStream_t s);
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
-                            double* work1, double* work2, cudaStream_t s);
+                            double* work1, double* work2, cudaStream_t s, float* Kd_dev = nullptr);
 size_t tensor_work_elems(const int grid[3], const int L[3]);
 
 // Energy (energy.cu): E[0..4] into out_dev (5 doubles, device); partials is

@@ -225,6 +225,27 @@ __global__ void k_tz(int nz, int Hx, int Hy, int Lz, int Hz, double scale, const
     Kt[t] = (float)((offdiag ? scale : -scale) * acc);
 }
 
+// 2-D (x, y) spectrum per z offset for the direct z sum: with
+// N2 = the x and y transforms of N (sine sums for odd axes, without their
+// factor -i), the (x, y) DFT of K = -N is -(-i)^(ox+oy) N2.  The kernel
+// works with M_z' = i M_z and H_z' = i H_z, which makes every coupling real:
+// stored d_c = s_c N2_c / (Lx Ly) with s = (-1, +1, +1, -1, +1, -1) for
+// (xx, xy, xz, yy, yz, zz); H_z' takes -d_xz, -d_yz.  Layout
+// Kd[kx][ky][dz][c], dz = 0..nz-1 (negative offsets: xz, yz change sign).
+__global__ void k_pack2d(int nz, int Hx, int Hy, double scale, const double* __restrict__ in,
+                         float* __restrict__ Kd) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)6 * Hx * Hy * nz;
+    if (t >= total) return;
+    const int c = (int)(t % 6);
+    const int dz = (int)((t / 6) % nz);
+    const int ky = (int)((t / ((size_t)6 * nz)) % Hy);
+    const int kx = (int)(t / ((size_t)6 * nz * Hy));
+    const double v = in[(((size_t)c * nz + dz) * Hy + ky) * Hx + kx];
+    const double sg = (c == 0 || c == 3 || c == 5) ? -1.0 : 1.0;
+    Kd[t] = (float)(sg * scale * v);
+}
+
 // Roots and weights of the n-point Gauss-Legendre rule on [-1, 1] by Newton
 // iteration on the three-term recurrence of the Legendre polynomials.
 static void gauss_legendre(int n, double* x, double* w) {
@@ -293,7 +314,7 @@ size_t tensor_work_elems(const int grid[3], const int L[3]) {
 }
 
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
-                            double* work1, double* work2, cudaStream_t s) {
+                            double* work1, double* work2, cudaStream_t s, float* Kd_dev) {
     const int nx = grid[0], ny = grid[1], nz = grid[2];
     const int Hx = L[0] / 2 + 1, Hy = L[1] / 2 + 1, Hz = L[2] / 2 + 1;
     double2* cs = nullptr;
@@ -308,6 +329,10 @@ cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_d
     k_tx<<<(unsigned)((n1 + T - 1) / T), T, 0, s>>>(nx, nz * ny, L[0], Hx, N_dev, work1, csx);
     size_t n2 = (size_t)6 * nz * Hy * Hx;
     k_ty<<<(unsigned)((n2 + T - 1) / T), T, 0, s>>>(ny, nz, Hx, L[1], Hy, work1, work2, csy);
+    if (Kd_dev) {
+        const size_t nd = (size_t)6 * Hx * Hy * nz;
+        k_pack2d<<<(unsigned)((nd + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, 1.0 / ((double)L[0] * L[1]), work2, Kd_dev);
+    }
     size_t n3 = (size_t)6 * Hx * Hy * Hz;
     const double scale = 1.0 / ((double)L[0] * L[1] * L[2]);
     k_tz<<<(unsigned)((n3 + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, L[2], Hz, scale, work2, Kt_dev, csz);
