@@ -54,6 +54,13 @@ enum {
 
 typedef struct mm_ctx mm_ctx;
 
+/* Integrators for mm_step (mm_set_integrator). */
+enum {
+    MM_INTEGRATOR_EULER = 0,   /* forward Euler, the paper's scheme (default)   */
+    MM_INTEGRATOR_HEUN = 1,    /* explicit trapezoid, second order              */
+    MM_INTEGRATOR_RK4 = 2      /* classic Runge-Kutta, fourth order             */
+};
+
 /*
  * mm_create -- build a solver context; the tensor set-up happens here, once
  * (Sec. 3: the tensor FFT "carried out at the beginning of simulation").
@@ -83,6 +90,17 @@ int mm_create(mm_ctx **out, const int grid[3], const double cell[3],
 
 /* mm_destroy -- free every resource of ctx.  NULL-safe.  Synchronises. */
 int mm_destroy(mm_ctx *ctx);
+
+/*
+ * mm_set_integrator -- choose the time stepper of mm_step.  Forward Euler
+ * (Table 1 caption) is the default and runs as the two-kernel step on
+ * power-of-two grids.  Heun and classic RK4 go beyond the paper: each stage
+ * evaluates H_eff of the stage state with the same three demag/field passes,
+ * stage states are not renormalised, the new state is renormalised to
+ * |M| = Ms.  They allocate two extra 3*N float32 buffers on first use.
+ * Returns MM_EINVAL for an unknown method, MM_ENOMEM on allocation failure.
+ */
+int mm_set_integrator(mm_ctx *ctx, int method);
 
 /* mm_set_field -- uniform external (Zeeman) field H_ext in A/m (Eq. (1),
  * (2)); applies to later steps.  H_ext: 3 doubles, host memory. */
@@ -114,11 +132,14 @@ int mm_demag_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
 int mm_effective_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
 
 /*
- * mm_step -- n forward-Euler steps of Eq. (6) of size dt on the resident M:
- * M <- Ms * (M + dt f(M)) / |M + dt f(M)|, every field term at M^n.  Each
- * step is three kernels (x R2C; per-kx-plane y/z FFT + tensor product +
- * inverse y/z; inverse x C2R fused with exchange, anisotropy, Zeeman, LLG,
- * Euler and renormalisation) replayed from CUDA graphs.  n >= 0, dt > 0.
+ * mm_step -- n steps of Eq. (6) of size dt on the resident M with the
+ * chosen integrator (default forward Euler:
+ * M <- Ms * (M + dt f(M)) / |M + dt f(M)|, every field term at M^n).  An
+ * Euler step is three kernels (x R2C; per-kx-plane y/z FFT + tensor product
+ * + inverse y/z; inverse x C2R fused with exchange, anisotropy, Zeeman, LLG,
+ * Euler and renormalisation), two on power-of-two grids where the next
+ * step's x R2C is fused into the update kernel; steps are replayed from
+ * CUDA graphs.  n >= 0, dt > 0.
  * Asynchronous: a non-finite result is reported by mm_sync / mm_energy.
  */
 int mm_step(mm_ctx *ctx, int n, double dt);

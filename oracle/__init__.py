@@ -14,7 +14,8 @@ Modules
              zero-padded FFT convolution (Eqs. (8)-(10), (13)-(16)).
   llg     -- exchange (Eqs. (3)-(4)), anisotropy (Eq. (5)), Zeeman, LLG
              right-hand side (Eq. (6)), forward Euler + renormalisation,
-             energy (Eq. (1)), macrospin closed form.
+             Heun and classic RK4 steps, energy (Eq. (1)), macrospin
+             closed form.
 
 All arithmetic is float64.  Every function is pinned by a ``-m "not gpu"``
 test against something other than itself (closed forms, brute force,
@@ -26,4 +27,4 @@ from .tensor import (newell_f, newell_g, newell_tensor, quadrature_tensor,
 from .demag import (wrap_pad_kernel, kernel_spectrum, demag_fft, demag_brute,
                     demag_at_cells)
 from .llg import (h_exchange, h_anisotropy, h_effective, llg_rhs, euler_step,
-                  run_euler, energy_terms, macrospin_closed_form)
+                  run_euler, rk_step, run_rk, energy_terms, macrospin_closed_form)

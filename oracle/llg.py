@@ -66,6 +66,43 @@ def euler_step(M, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
     return Mn, Hd
 
 
+def _rhs(M, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
+    H = h_effective(M, cell, Ms, A, Ku, H_ext, demag_fft(M, Kt, L))
+    return llg_rhs(M, H, Ms, alpha, gamma)
+
+
+def rk_step(M, dt, method, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
+    """One explicit Runge-Kutta step of Eq. (6), the paper's Euler scheme
+    replaced by a higher-order one (beyond the paper).  Stage states are
+    plain (not renormalised); the new state is renormalised to |M| = Ms as
+    in the Euler step.
+      heun: k1 = f(M), k2 = f(M + dt k1), M' = M + dt (k1 + k2)/2
+      rk4:  k1 = f(M), k2 = f(M + dt/2 k1), k3 = f(M + dt/2 k2),
+            k4 = f(M + dt k3), M' = M + dt (k1 + 2 k2 + 2 k3 + k4)/6"""
+    f = lambda X: _rhs(X, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)
+    if method == "euler":
+        Mn = M + dt * f(M)
+    elif method == "heun":
+        k1 = f(M)
+        k2 = f(M + dt * k1)
+        Mn = M + 0.5 * dt * (k1 + k2)
+    elif method == "rk4":
+        k1 = f(M)
+        k2 = f(M + 0.5 * dt * k1)
+        k3 = f(M + 0.5 * dt * k2)
+        k4 = f(M + dt * k3)
+        Mn = M + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    else:
+        raise ValueError(method)
+    return Mn * (Ms / np.sqrt(np.sum(Mn * Mn, axis=0)))
+
+
+def run_rk(M, nsteps, dt, method, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
+    for _ in range(nsteps):
+        M = rk_step(M, dt, method, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)
+    return M
+
+
 def run_euler(M, nsteps, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
     for _ in range(nsteps):
         M, _ = euler_step(M, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)

@@ -177,6 +177,7 @@ cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem3);
         if (e != cudaSuccess) return e;
     }
+    if (l.split) return configure_split_kernels(g);
     if (l.fp) return cudaFuncSetAttribute(l.fp->pl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.fp->s2);
     PlaneFn pf = plane_fn(g.Lz);
     if (!pf) return cudaErrorInvalidValue;
@@ -194,6 +195,7 @@ cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2*
 }
 
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s) {
+    if (l.split) return launch_split_plane(g, S, s);
     if (l.fp) {
         l.fp->pl<<<g.Hx, l.fp->t2, l.fp->s2, s>>>(g, S);
         return cudaGetLastError();

@@ -63,6 +63,9 @@ struct mm_ctx {
     FastStepFns fs;            // two-kernel step (power-of-two grids)
     bool has_fs = false;
     float2* S2 = nullptr;      // second spectrum buffer of the two-kernel step
+    int method = MM_INTEGRATOR_EULER;
+    float* Mst = nullptr;      // Runge-Kutta stage state
+    float* acc = nullptr;      // Runge-Kutta weighted slope sum
     bool spec_valid = false;   // S[cur] (S or S2) holds the x half-spectrum of M[cur]
 };
 
@@ -117,8 +120,6 @@ static int build_plan(mm_ctx* c) {
     g.Jst = g.ny;
     if (!make_axis_plan(g.Lx, &g.px) || !make_axis_plan(g.Ly, &g.py) || !make_axis_plan(g.Lz, &g.pz))
         return fail(MM_EUNSUPPORTED, "no radix plan for padded lengths %d %d %d", g.Lx, g.Ly, g.Lz);
-    if (g.nz > kMaxPlaneNz || !plane_supported_lz(g.Lz))
-        return fail(MM_EUNSUPPORTED, "nz = %d: only nz <= %d is planned", g.nz, kMaxPlaneNz);
 
     // Each pass holds its lines plus a Stockham ping-pong scratch in shared
     // memory (fft_lines); `g*` is the number of lines per scratch group.
@@ -141,15 +142,24 @@ static int build_plan(mm_ctx* c) {
     l.t3 = 256;
     l.g3 = 3 * l.r3 / 2;
     l.smem3 = (size_t)2 * l.g3 * lx_bytes;
-    // pass 2: one kx plane of 3*nz lines of Ly, scratch for g2 of them
+    // pass 2: one kx plane of 3*nz lines of Ly in shared memory (+ scratch
+    // for g2 of them), or, for thick samples, the split y / z / y kernels
+    // with the spectrum row stride widened to Ly.
     const int nl2 = 3 * g.nz;
     l.t2 = (nl2 * g.Ly >= 4096) ? 512 : 256;
     const size_t plane_bytes = (size_t)nl2 * ly_bytes;
-    if (plane_bytes + ly_bytes > smem_cap)
-        return fail(MM_EUNSUPPORTED, "kx plane of %zu bytes exceeds shared memory", plane_bytes);
-    size_t fit = (smem_cap - plane_bytes) / ly_bytes;
-    l.g2 = (int)(fit < (size_t)nl2 ? fit : (size_t)nl2);
-    l.smem2 = plane_bytes + (size_t)l.g2 * ly_bytes;
+    l.split = g.nz > kMaxPlaneNz || !plane_supported_lz(g.Lz) || plane_bytes + 2 * ly_bytes > 200 * 1024;
+    if (l.split) {
+        g.Jst = g.Ly;
+        l.g2 = 0;
+        l.smem2 = 0;
+        if (split_smem_y(g) > smem_cap || split_smem_z(g) > smem_cap)
+            return fail(MM_EUNSUPPORTED, "padded lengths %d, %d too long for the split pass", g.Ly, g.Lz);
+    } else {
+        size_t fit = (smem_cap - plane_bytes) / ly_bytes;
+        l.g2 = (int)(fit < (size_t)nl2 ? fit : (size_t)nl2);
+        l.smem2 = plane_bytes + (size_t)l.g2 * ly_bytes;
+    }
     if (l.smem1 > smem_cap || l.smem3 > smem_cap)
         return fail(MM_EUNSUPPORTED, "x lines of %zu bytes exceed shared memory", lx_bytes);
 
@@ -171,11 +181,11 @@ static int build_plan(mm_ctx* c) {
             case 8: pl = fast_lookup_plane_nz8(g.ny, &f); break;
             default: break;
         }
-        if (pl && f.s2 <= smem_cap) l.fp = &f;
+        if (pl && f.s2 <= smem_cap && !l.split) l.fp = &f;
         FastStepFns& s = c->fs;
         bool ok = fast_step_lookup_x(g.nx, &s);
         ok = ok && (fast_step_lookup_plane_a(g.ny, g.nz, &s) || fast_step_lookup_plane_b(g.ny, g.nz, &s));
-        ok = ok && l.fx && g.ny % s.rb == 0 && s.sa <= smem_cap && s.sb <= smem_cap;
+        ok = ok && l.fx && !l.split && g.ny % s.rb == 0 && s.sa <= smem_cap && s.sb <= smem_cap;
         c->has_fs = ok;
     }
     return MM_OK;
@@ -217,6 +227,8 @@ static void release(mm_ctx* c) {
     cudaFree(c->Mbuf[0]);
     cudaFree(c->Mbuf[1]);
     cudaFree(c->H);
+    cudaFree(c->Mst);
+    cudaFree(c->acc);
     cudaFree(c->flag);
     cudaFree(c->partials);
     cudaFree(c->Edev);
@@ -345,6 +357,23 @@ extern "C" int mm_destroy(mm_ctx* c) {
     return MM_OK;
 }
 
+extern "C" int mm_set_integrator(mm_ctx* c, int method) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    if (method != MM_INTEGRATOR_EULER && method != MM_INTEGRATOR_HEUN && method != MM_INTEGRATOR_RK4)
+        return fail(MM_EINVAL, "unknown integrator %d", method);
+    if (method != MM_INTEGRATOR_EULER && !c->Mst) {
+        const size_t n = 3 * (size_t)c->g.N;
+        CU(cudaMalloc(&c->Mst, sizeof(float) * n));
+        CU(cudaMalloc(&c->acc, sizeof(float) * n));
+    }
+    if (method != c->method) {
+        c->method = method;
+        c->ver++;                               // re-capture the step graphs
+        c->spec_valid = false;
+    }
+    return MM_OK;
+}
+
 extern "C" int mm_set_field(mm_ctx* c, const double H_ext[3]) {
     if (!c || !H_ext) return fail(MM_EINVAL, "null argument");
     for (int a = 0; a < 3; ++a)
@@ -409,7 +438,29 @@ static float2* spec(mm_ctx* c, int p) { return p == 0 ? c->S : c->S2; }
 // One step from parity p (M[p] -> M[1-p]).  Two-kernel path: K_A on S[p],
 // K_B into S[1-p], programmatic dependent launch between them.  Generic
 // path: the three passes on S.
+// One explicit Runge-Kutta step (Heun or classic RK4) from parity p: per
+// stage a field evaluation into H, then the stage update.
+static int enqueue_rk_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
+    static const float heun_a[2] = {1.f, 0.f}, heun_b[2] = {0.5f, 0.5f};
+    static const float rk4_a[4] = {0.5f, 0.5f, 1.f, 0.f};
+    static const float rk4_b[4] = {1.f / 6.f, 1.f / 3.f, 1.f / 3.f, 1.f / 6.f};
+    const int ns = c->method == MM_INTEGRATOR_HEUN ? 2 : 4;
+    const float* av = ns == 2 ? heun_a : rk4_a;
+    const float* bv = ns == 2 ? heun_b : rk4_b;
+    const LlgCoef cf = make_coef(c, dt);
+    for (int st = 0; st < ns; ++st) {
+        const float* Min = st == 0 ? c->Mbuf[p] : c->Mst;
+        int rc = run_passes(c, kModeHeff, Min, c->H, dt, s);
+        if (rc != MM_OK) return rc;
+        const int kind = st == 0 ? 0 : (st == ns - 1 ? 2 : 1);
+        float* out = kind == 2 ? c->Mbuf[1 - p] : c->Mst;
+        CU(launch_rk_stage(c->g.N, cf, av[st], bv[st], kind, Min, c->H, c->Mbuf[p], c->acc, out, c->flag, s));
+    }
+    return MM_OK;
+}
+
 static int enqueue_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
+    if (c->method != MM_INTEGRATOR_EULER) return enqueue_rk_step(c, p, dt, s);
     if (c->has_fs) {
         CU(launch_step_pdl(c->g, c->fs, make_coef(c, dt), spec(c, p), spec(c, 1 - p), c->Mbuf[p], c->Mbuf[1 - p],
                            c->flag, s, true));
@@ -443,7 +494,7 @@ static int capture_step(mm_ctx* c, int p, double dt) {
 
 // Form S[cur] from M[cur] when the two-kernel step needs it.
 static int ensure_spectrum(mm_ctx* c) {
-    if (!c->has_fs || c->spec_valid) return MM_OK;
+    if (!c->has_fs || c->spec_valid || c->method != MM_INTEGRATOR_EULER) return MM_OK;
     CU(launch_pass1(c->g, c->l, c->Mbuf[c->cur], spec(c, c->cur), c->stream));
     c->spec_valid = true;
     return MM_OK;
@@ -510,7 +561,7 @@ extern "C" int mm_plan_info(const mm_ctx* c, int L[3]) {
         L[1] = c->g.Ly;
         L[2] = c->g.Lz;
     }
-    return c->has_fs ? 2 : 3;
+    return c->has_fs ? 2 : (c->l.split ? 5 : 3);
 }
 
 extern "C" int mm_tensor_octant(mm_ctx* c, double* out) {

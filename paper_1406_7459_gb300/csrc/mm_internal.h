@@ -52,6 +52,7 @@ struct Launch {
     size_t smem1, smem2, smem3;
     const FastFns* fx = nullptr;     // compile-time x passes, if the grid has them
     const FastFns* fp = nullptr;     // compile-time plane kernel, if available
+    bool split = false;              // pass 2 as y / z / y kernels (thick samples)
 };
 
 enum Pass3Mode { kModeDemag = 0, kModeHeff = 1, kModeStep = 2 };
@@ -105,6 +106,17 @@ cudaError_t configure_step_kernels(const FastStepFns& f);
 cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, float2* S, cudaStream_t s, bool pdl);
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* S, float2* Snext,
                           const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
+
+// Pass 2 for thick samples (split_kernels.cu); the spectrum row stride is Ly.
+cudaError_t launch_split_plane(const Geom& g, float2* S, cudaStream_t s);
+cudaError_t configure_split_kernels(const Geom& g);
+size_t split_smem_y(const Geom& g);
+size_t split_smem_z(const Geom& g);
+
+// Runge-Kutta stage update (integrators.cu).  kind: 0 first stage, 1 middle
+// stage, 2 last stage (writes the renormalised new state).
+cudaError_t launch_rk_stage(int N, const LlgCoef& cf, float a_next, float b_acc, int kind, const float* Mst,
+                            const float* H, const float* Mb, float* acc, float* out, int* flag, cudaStream_t s);
 
 // Tensor set-up (tensor_setup.cu).  Writes N (FP64 octant) and/or Kt.
 cudaError_t tensor_octant_fp64(const int grid[3], const double cell[3], double* N_dev, cudaStream_t s);

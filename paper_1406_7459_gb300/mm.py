@@ -22,6 +22,10 @@ MM_ENONFINITE = -4
 MM_ETIMEOUT = -5
 MM_EUNSUPPORTED = -6
 
+MM_INTEGRATOR_EULER = 0
+MM_INTEGRATOR_HEUN = 1
+MM_INTEGRATOR_RK4 = 2
+
 # every function declared in include/mm.h, with (restype, argtypes)
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 _PROTOS = {
@@ -29,6 +33,7 @@ _PROTOS = {
                            _c_double, _c_double, _c_double, _c_double, _c_double, _vp]),
     "mm_destroy": (_c_int, [_vp]),
     "mm_set_field": (_c_int, [_vp, ctypes.POINTER(_c_double)]),
+    "mm_set_integrator": (_c_int, [_vp, _c_int]),
     "mm_set_m": (_c_int, [_vp, _vp]),
     "mm_get_m": (_c_int, [_vp, _vp]),
     "mm_demag_field": (_c_int, [_vp, _vp, _vp]),
@@ -131,6 +136,12 @@ def mm_destroy(ctx):
     h, ctx.handle = ctx.handle, None
     if h:
         _check(lib().mm_destroy(h))
+
+
+def mm_set_integrator(ctx, method):
+    if isinstance(method, str):
+        method = {"euler": MM_INTEGRATOR_EULER, "heun": MM_INTEGRATOR_HEUN, "rk4": MM_INTEGRATOR_RK4}[method]
+    _check(lib().mm_set_integrator(ctx.handle, int(method)))
 
 
 def mm_set_field(ctx, H_ext):

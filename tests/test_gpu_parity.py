@@ -281,7 +281,7 @@ def test_argument_errors_on_gpu():
     with pytest.raises(_mm().MMError):
         _mm().mm_step(ctx, 1, -1e-13)
     with pytest.raises(_mm().MMError) as e:
-        _mm().mm_create((8, 8, 9), cell, MS, A_EX, 0.0, 0.5, GAMMA)
+        _mm().mm_create((3000, 8, 1), cell, MS, A_EX, 0.0, 0.5, GAMMA)   # padded x length > 4096
     assert e.value.code == _mm().MM_EUNSUPPORTED
 
 
@@ -351,3 +351,59 @@ def test_steps_interleaved_with_other_calls(grid):
     _mm().mm_sync(ctx)
     assert rel_l2(_host(out, grid) - M2, ref - M2) < 1e-4
     assert rel_l2(_host(out, grid), ref) < 1e-6
+
+
+THICK_GRIDS = [(8, 8, 9), (20, 12, 10), (16, 16, 16), (32, 32, 32), (24, 10, 12)]
+
+
+@pytest.mark.parametrize("grid", THICK_GRIDS)
+def test_thick_samples_split_pass(grid):
+    """nz > 8: pass 2 runs as separate y / z / y kernels."""
+    cell = (4e-9, 4e-9, 4e-9)
+    M = inputs.random_unit_m(grid, MS, seed=51)
+    ctx = _ctx(grid, cell, Ku=1e4, alpha=0.3)
+    assert _mm().mm_plan_info(ctx)[1] == 5
+    Md = _dev(M)
+    Hd = torch.empty_like(Md)
+    _mm().mm_demag_field(ctx, Md, Hd)
+    Kt, Lp = oracle_spectrum(grid, cell)
+    M64 = M.astype(np.float64)
+    Href = D.demag_fft(M64, Kt, Lp)
+    assert rel_l2(_host(Hd, grid), Href) < 1e-5
+    assert rel_max(_host(Hd, grid), Href) < 1e-5
+    _mm().mm_set_m(ctx, Md)
+    _mm().mm_step(ctx, 3, 5e-14)
+    out = torch.empty_like(Md)
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    ref = L.run_euler(M64, 3, 5e-14, cell, MS, A_EX, 1e4, 0.3, GAMMA, (0, 0, 0), Kt, Lp)
+    assert rel_l2(_host(out, grid), ref) < 1e-5
+
+
+@pytest.mark.parametrize("method", ["heun", "rk4"])
+@pytest.mark.parametrize("grid", [(20, 12, 3), (32, 32, 2), (64, 64, 4)])
+def test_runge_kutta_steps_match_oracle(method, grid):
+    cell = (4e-9, 4e-9, 3e-9)
+    Ku, alpha, dt, Hext = 1e4, 0.2, 1e-13, (2e4, -1e4, 5e3)
+    M = inputs.random_unit_m(grid, MS, seed=61)
+    ctx = _ctx(grid, cell, Ku=Ku, alpha=alpha)
+    _mm().mm_set_integrator(ctx, method)
+    _mm().mm_set_field(ctx, Hext)
+    _mm().mm_set_m(ctx, _dev(M))
+    _mm().mm_step(ctx, 5, dt)
+    out = torch.empty(3 * ctx.N, device="cuda")
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    Kt, Lp = oracle_spectrum(grid, cell)
+    ref = L.run_rk(M.astype(np.float64), 5, dt, method, cell, MS, A_EX, Ku, alpha, GAMMA, Hext, Kt, Lp)
+    got = _host(out, grid)
+    assert rel_l2(got - M, ref - M) < 1e-4
+    assert rel_l2(got, ref) < 1e-5
+    # switching back to Euler gives the Euler trajectory again
+    _mm().mm_set_integrator(ctx, "euler")
+    _mm().mm_set_m(ctx, _dev(M))
+    _mm().mm_step(ctx, 2, dt)
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    ref_e = L.run_euler(M.astype(np.float64), 2, dt, cell, MS, A_EX, Ku, alpha, GAMMA, Hext, Kt, Lp)
+    assert rel_l2(_host(out, grid), ref_e) < 1e-5

@@ -133,3 +133,41 @@ def test_undamped_energy_drift_is_first_order():
         M = L.run_euler(M0, n, dt, cell, Ms, A, Ku, 0.0, gamma, (0, 0, 0), Kt, Lp)
         drift.append(abs(_energy(M, cell, Ms, A, Ku, (0, 0, 0), Kt, Lp) - E0))
     assert 1.6 < drift[0] / drift[1] < 2.4, drift
+
+
+def _macrospin_rk(method, dt, t_end, theta0, phi0, Hz, alpha, gamma, Ms):
+    cell = (3e-9, 3e-9, 3e-9)
+    grid = (1, 1, 1)
+    Lp = D.default_lengths(grid)
+    Kt = D.kernel_spectrum(T.tensor_octant(grid, cell), Lp)
+    M = Ms * np.array([np.sin(theta0) * np.cos(phi0), np.sin(theta0) * np.sin(phi0),
+                       np.cos(theta0)]).reshape(3, 1, 1, 1)
+    n = int(round(t_end / dt))
+    M = L.run_rk(M, n, dt, method, cell, Ms, 1.3e-11, 0.0, alpha, gamma, (0.0, 0.0, Hz), Kt, Lp)
+    return M.reshape(3) / Ms
+
+
+@pytest.mark.parametrize("method,order", [("euler", 1), ("heun", 2), ("rk4", 4)])
+def test_runge_kutta_orders_on_the_macrospin(method, order):
+    """Error against the closed-form solution of Eq. (6) falls as dt^order."""
+    theta0, phi0, Hz, alpha, gamma, Ms = 1.2, 0.3, 2e5, 0.1, 2.211e5, 8.6e5
+    t_end = 2e-10
+    th, ph = L.macrospin_closed_form(theta0, phi0, Hz, alpha, gamma, t_end)
+    exact = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    dts = (8e-13, 4e-13, 2e-13) if order == 4 else (4e-14, 2e-14, 1e-14)
+    errs = [np.linalg.norm(_macrospin_rk(method, dt, t_end, theta0, phi0, Hz, alpha, gamma, Ms) - exact)
+            for dt in dts]
+    ratios = [a / b for a, b in zip(errs[:-1], errs[1:])]
+    for r in ratios:
+        assert 0.8 * 2 ** order < r < 1.25 * 2 ** order, (errs, ratios)
+
+
+def test_rk_euler_branch_equals_euler_step():
+    grid, cell = (5, 4, 2), (5e-9, 5e-9, 3e-9)
+    Ms, A, Ku, alpha, gamma, Hext = 8.6e5, 1.3e-11, 1e4, 0.3, 2.211e5, (1e4, 0, 0)
+    Lp = D.default_lengths(grid)
+    Kt = D.kernel_spectrum(T.tensor_octant(grid, cell), Lp)
+    M = inputs.random_unit_m(grid, Ms, seed=3).astype(np.float64)
+    a = L.rk_step(M, 1e-13, "euler", cell, Ms, A, Ku, alpha, gamma, Hext, Kt, Lp)
+    b, _ = L.euler_step(M, 1e-13, cell, Ms, A, Ku, alpha, gamma, Hext, Kt, Lp)
+    assert np.max(np.abs(a - b)) < 1e-9 * Ms
