@@ -339,12 +339,121 @@ def run_gpu(args, rank, ws):
     return 0
 
 
+def run_cube(args, rank, ws):
+    """Per-step time of the N^3 cube (N = 8..128) beside the paper's Table 1
+    (context only: other hardware, other precision, a graphics-API path)."""
+    import torch
+    from paper_1406_7459_gb300 import mm, inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = inputs.CUBE
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_table1.json")))
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    points = []
+    for n in inputs.CUBE_SIZES:
+        grid = (n, n, n)
+        ctx = mm.mm_create(grid, w["cell"], w["Ms"], w["A"], w["Ku"], w["alpha"], w["gamma"])
+        mm.mm_set_m(ctx, torch.from_numpy(inputs.random_unit_m(grid, w["Ms"], w["seed"]).reshape(-1)).cuda())
+        mm.mm_step(ctx, max(args.warmup, 3), w["dt"])
+        torch.cuda.synchronize()
+        K = max(20, min(args.steps, 200))
+        tot = 0.0
+        for s in range(K):
+            flush.fill_(float(s))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            mm.mm_step(ctx, 1, w["dt"])
+            b.record()
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        mm.mm_sync(ctx)
+        ms = tot / K
+        i = table["N"].index(n)
+        points.append({"N": n, "cells": n ** 3, "ms_per_step": ms, "cells_steps_per_s": n ** 3 / (ms * 1e-3),
+                       "launches_per_step": mm.mm_plan_info(ctx)[1],
+                       "paper_gpu_ms": table["gpu_ms"][i], "paper_cpu_ms": table["cpu_ms"][i],
+                       "vs_paper_gpu": table["gpu_ms"][i] / ms})
+        mm.mm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps({"workload": "cube N^3, 4 nm cells, Ku 5e2 easy x, alpha 0.5, random start, Euler "
+                                      "dt 5e-14 s, L2 flushed before every timed step",
+                          "metric": "ms per Euler step", "dtype": "f32", "data": "synthetic",
+                          "points": points,
+                          "paper_context": table["source"] + "; " + table["hardware"]["gpu"]}))
+    return 0
+
+
+def run_batch(args, rank, ws):
+    """512 independent samples of uneven size (nx 16..256, ny 16..64,
+    nz 1..2, random Ku, H_ext, alpha) stepped as one batch after the tile
+    autotuner, against the same samples stepped one context at a time.  The
+    batch working set (~0.7 GB) exceeds L2, so steps run back to back."""
+    import torch
+    from paper_1406_7459_gb300 import mm, inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    samples = inputs.batch_samples(512, seed=3)
+    dt = 5e-14
+    b = mm.mm_batch_create([s["grid"] for s in samples], [s["cell"] for s in samples],
+                           [s["Ms"] for s in samples], [s["A"] for s in samples], [s["Ku"] for s in samples],
+                           [s["alpha"] for s in samples], [s["gamma"] for s in samples])
+    mm.mm_batch_set_field(b, [s["H_ext"] for s in samples])
+    M = np.concatenate([s["M"].reshape(-1) for s in samples])
+    mm.mm_batch_set_m(b, torch.from_numpy(M).cuda())
+    choice, tune_ms = mm.mm_batch_autotune(b, dt)
+    cells = mm.mm_batch_cells(b)
+    K = max(10, min(args.steps, 200))
+    mm.mm_batch_step(b, max(args.warmup, 3), dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    mm.mm_batch_step(b, K, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    mm.mm_batch_sync(b)
+    batch_ms = e0.elapsed_time(e1) / K
+    # the same samples, one context each, stepped one after another
+    ctxs = []
+    for s in samples:
+        c = mm.mm_create(s["grid"], s["cell"], s["Ms"], s["A"], s["Ku"], s["alpha"], s["gamma"])
+        mm.mm_set_field(c, s["H_ext"])
+        mm.mm_set_m(c, torch.from_numpy(s["M"].reshape(-1)).cuda())
+        mm.mm_step(c, 3, dt)
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    Ks = max(5, K // 10)
+    e0.record()
+    for _ in range(Ks):
+        for c in ctxs:
+            mm.mm_step(c, 1, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1) / Ks
+    for c in ctxs:
+        mm.mm_destroy(c)
+    if rank == 0:
+        print(json.dumps({"workload": "batch of 512 samples, nx 16..256, ny 16..64, nz 1..2, Ku U[0,1e4], "
+                                      "|H_ext| U[0,5e4] random direction, alpha U[0.01,0.5], Euler dt 5e-14 s",
+                          "metric": "cells*steps/s over the batch", "dtype": "f32", "data": "synthetic",
+                          "cells": cells, "batched_ms_per_step": batch_ms,
+                          "batched_cells_steps_per_s": cells / (batch_ms * 1e-3),
+                          "one_context_at_a_time_ms_per_step": single_ms,
+                          "one_context_at_a_time_cells_steps_per_s": cells / (single_ms * 1e-3),
+                          "batching_gain": single_ms / batch_ms,
+                          "autotune_choice": {"rows_pass1": choice[0], "rows_pass3": choice[1],
+                                              "threads": choice[2]},
+                          "autotune_ms_per_candidate": tune_ms,
+                          "l2": "working set larger than L2; steps back to back"}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="film", choices=["film", "cube", "batch"],
+                    help="film: the 256x256x4 benchmark line; cube: the N^3 per-step curve; "
+                         "batch: 512 uneven samples batched vs one at a time")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
@@ -355,6 +464,10 @@ def main():
     rank, ws = dist_setup()
     if args.impl == "reference":
         rc = run_reference(args, rank, ws)
+    elif args.workload == "cube":
+        rc = run_cube(args, rank, ws)
+    elif args.workload == "batch":
+        rc = run_batch(args, rank, ws)
     else:
         rc = run_gpu(args, rank, ws)
     if ws > 1:

@@ -201,6 +201,40 @@ int mm_kernel_spectrum(mm_ctx *ctx, float *out);
 int mm_time_passes(mm_ctx *ctx, int reps, double dt, void *flush, unsigned long long flush_bytes,
                    float ms[3]);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent samples of uneven size stepped together (not in
+ * the paper, whose runs are one sample at a time; its Sec. 4 blames small-
+ * size slowness on launch overhead, which batching removes).  Sample s has
+ * its own grid (nz <= 4), cell, material, field and tensor spectrum; every
+ * call of mm_batch_step advances all samples by forward-Euler steps of the
+ * same dt, with three batched kernels per step replayed from a CUDA graph.
+ * M arrays of a batch are the samples' SoA blocks back to back (sample s
+ * starts at float offset sum_{t<s} 3 N_t).
+ * ------------------------------------------------------------------------ */
+typedef struct mm_batch mm_batch;
+
+/* grids: 3n ints; cells: 3n doubles (m); Ms, A, Ku, alpha, gamma: n doubles
+ * each, same meaning as in mm_create.  Initial M uniform +x, H_ext = 0.
+ * Synchronises.  MM_EINVAL / MM_EUNSUPPORTED / MM_ENOMEM / MM_ECUDA. */
+int mm_batch_create(mm_batch **out, int n, const int *grids, const double *cells, const double *Ms,
+                    const double *A, const double *Ku, const double *alpha, const double *gamma,
+                    void *cuda_stream);
+int mm_batch_destroy(mm_batch *b);                       /* NULL-safe */
+int mm_batch_set_field(mm_batch *b, const double *H_ext); /* 3n doubles, A/m */
+int mm_batch_set_m(mm_batch *b, const float *M);          /* host or device; synchronises */
+int mm_batch_get_m(mm_batch *b, float *M);                /* host or device; synchronises */
+int mm_batch_step(mm_batch *b, int n, double dt);         /* asynchronous */
+int mm_batch_sync(mm_batch *b);                           /* MM_ENONFINITE if any step failed */
+long long mm_batch_cells(const mm_batch *b);              /* total cells, or -1 */
+/*
+ * mm_batch_autotune -- time the candidate tile shapes (rows per CTA of the
+ * x passes, threads per CTA) on this batch with steps of size dt, keep the
+ * fastest, and restore the state (tuning does not advance the samples).
+ * choice (may be NULL): {rows pass 1, rows pass 3, threads}; ms_out (may be
+ * NULL): 12 floats, mean ms per step of each candidate.  Synchronises.
+ */
+int mm_batch_autotune(mm_batch *b, double dt, int choice[3], float *ms_out);
+
 /*
  * mm_demag_field_noalloc -- H_demag of M, like mm_demag_field, for callers
  * that cannot allocate device memory: for example a host program that

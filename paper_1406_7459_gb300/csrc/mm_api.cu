@@ -191,12 +191,23 @@ static int build_plan(mm_ctx* c) {
     return MM_OK;
 }
 
+// Planning helpers shared with the batched driver (batch.cu).
+namespace mmk {
+int plan_padded_length(int n) { return padded_length(n); }
+bool plan_axis(int L, AxisPlan* p) { return make_axis_plan(L, p); }
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace mmk
+
 static void host_twiddles(int L, float2* out) {
     for (int m = 0; m < L; ++m) {
         const double a = -2.0 * 3.14159265358979323846 * (double)m / (double)L;
         out[m] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
 }
+
+namespace mmk {
+void plan_twiddles(int L, float2* out) { host_twiddles(L, out); }
+}  // namespace mmk
 
 static LlgCoef make_coef(const mm_ctx* c, double dt) {
     LlgCoef f;

@@ -57,6 +57,12 @@ struct Launch {
 
 enum Pass3Mode { kModeDemag = 0, kModeHeff = 1, kModeStep = 2 };
 
+// Planning helpers (mm_api.cu), shared with the batched driver.
+int plan_padded_length(int n);
+bool plan_axis(int L, AxisPlan* p);
+void plan_twiddles(int L, float2* out);
+int set_error(int code, const char* msg);
+
 // Launchers (demag_passes.cu).  All asynchronous on `s`.
 cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s);
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s);
@@ -67,7 +73,6 @@ bool plane_supported_lz(int Lz);
 typedef void (*PlaneFn)(Geom, int, float2*);
 PlaneFn plane_fn_small(int Lz);   // plane_small.cu
 PlaneFn plane_fn_mid(int Lz);     // plane_mid.cu
-PlaneFn plane_fn_large(int Lz);   // plane_large.cu
 
 // Compile-time specialised kernels for power-of-two grids (fast_*.cu).
 struct FastFns {

@@ -44,9 +44,8 @@ __device__ __forceinline__ void small_dft(float2 (&a)[LZ], int nin, int nout, co
 }
 
 template <int LZ>
-__global__ void __launch_bounds__(512) k_plane(Geom g, int group, float2* __restrict__ S) {
+__device__ __forceinline__ void plane_body(const Geom& g, int group, float2* __restrict__ S, int kx) {
     extern __shared__ float2 sm[];
-    const int kx = blockIdx.x;
     const int lstride = padded_len(g.Ly);
     const int nz = g.nz;
     const int nl = 3 * nz;
@@ -101,6 +100,11 @@ __global__ void __launch_bounds__(512) k_plane(Geom g, int group, float2* __rest
         const int j = idx - l * g.ny;
         plane[(size_t)l * g.Jst + j] = sm[l * lstride + padi(j)];
     }
+}
+
+template <int LZ>
+__global__ void __launch_bounds__(512) k_plane(Geom g, int group, float2* __restrict__ S) {
+    plane_body<LZ>(g, group, S, blockIdx.x);
 }
 
 }  // namespace mmk

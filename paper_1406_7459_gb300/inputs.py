@@ -64,3 +64,31 @@ PRECISION_GRIDS = ((1024, 1024, 1), (256, 256, 64))
 PRECISION = dict(cell=(2.5e-9, 2.5e-9, 2.5e-9), Ms=8.6e5, A=1.3e-11, Ku=0.0,
                  alpha=0.5, gamma=GAMMA0, H_ext=(0.0, 0.0, 0.0), dt=5e-14,
                  steps=10000, seed=2, amplitude=0.1)
+
+# N x N x N cube relaxation, a synthetic stand-in for the paper's Table 1
+# workload (muMAG standard problem 3 is not reproduced): 4 nm cubic cells,
+# the size-sweep material, strong damping, seeded random start, no field.
+CUBE_SIZES = (8, 16, 32, 64, 128)
+CUBE = dict(cell=(4e-9, 4e-9, 4e-9), Ms=8.6e5, A=1.3e-11, Ku=5e2, alpha=0.5, gamma=GAMMA0,
+            H_ext=(0.0, 0.0, 0.0), dt=5e-14, seed=5)
+
+
+def batch_samples(n, seed=3, nx=(16, 256), ny=(16, 64), nz=(1, 2)):
+    """Independent samples of uneven size: nx ~ U{16..256}, ny ~ U{16..64},
+    nz ~ U{1, 2}, Ku ~ U[0, 1e4] J/m^3, |H_ext| ~ U[0, 5e4] A/m in a
+    direction uniform on the sphere, alpha ~ U[0.01, 0.5]; the thin-film
+    cell and material otherwise.  Returns a list of dicts with a seeded
+    random start M (float32, (3, nz, ny, nx))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n):
+        g = (int(rng.integers(nx[0], nx[1] + 1)), int(rng.integers(ny[0], ny[1] + 1)),
+             int(rng.integers(nz[0], nz[1] + 1)))
+        d = rng.standard_normal(3)
+        d /= np.sqrt(np.sum(d * d))
+        h = rng.uniform(0.0, 5e4) * d
+        out.append(dict(grid=g, cell=(5e-9, 5e-9, 3e-9), Ms=8.6e5, A=1.3e-11,
+                        Ku=float(rng.uniform(0.0, 1e4)), alpha=float(rng.uniform(0.01, 0.5)),
+                        gamma=GAMMA0, H_ext=tuple(float(v) for v in h),
+                        M=random_unit_m(g, 8.6e5, seed * 100003 + s)))
+    return out

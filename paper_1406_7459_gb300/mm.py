@@ -48,6 +48,18 @@ _PROTOS = {
     "mm_time_passes": (_c_int, [_vp, _c_int, _c_double, _vp, ctypes.c_ulonglong,
                                 ctypes.POINTER(ctypes.c_float)]),
     "mm_demag_field_noalloc": (_c_int, [ctypes.POINTER(_c_int), _vp, _vp, _vp, _vp]),
+    "mm_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_double),
+                                 ctypes.POINTER(_c_double), ctypes.POINTER(_c_double),
+                                 ctypes.POINTER(_c_double), ctypes.POINTER(_c_double),
+                                 ctypes.POINTER(_c_double), _vp]),
+    "mm_batch_destroy": (_c_int, [_vp]),
+    "mm_batch_set_field": (_c_int, [_vp, ctypes.POINTER(_c_double)]),
+    "mm_batch_set_m": (_c_int, [_vp, _vp]),
+    "mm_batch_get_m": (_c_int, [_vp, _vp]),
+    "mm_batch_step": (_c_int, [_vp, _c_int, _c_double]),
+    "mm_batch_sync": (_c_int, [_vp]),
+    "mm_batch_cells": (ctypes.c_longlong, [_vp]),
+    "mm_batch_autotune": (_c_int, [_vp, _c_double, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None
@@ -224,3 +236,72 @@ def mm_demag_field_noalloc(grid, Kt, M, H, stream=None):
     _check(lib().mm_demag_field_noalloc(g, _vp(_ptr(Kt)), _vp(_ptr(M, n)), _vp(_ptr(H, n)),
                                         _vp(_stream_handle(stream))))
     return H
+
+
+class Batch:
+    """Owned handle of an mm_batch."""
+
+    def __init__(self, handle, grids):
+        self.handle = handle
+        self.grids = [tuple(g) for g in grids]
+        self.sizes = [3 * g[0] * g[1] * g[2] for g in self.grids]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.total = int(self.offsets[-1])
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.mm_batch_destroy(h)
+
+
+def _darr(v):
+    v = [float(x) for x in v]
+    return (ctypes.c_double * len(v))(*v)
+
+
+def mm_batch_create(grids, cells, Ms, A, Ku, alpha, gamma, stream=None):
+    n = len(grids)
+    g = (ctypes.c_int * (3 * n))(*[int(v) for gr in grids for v in gr])
+    c = _darr([v for ce in cells for v in ce])
+    out = _vp()
+    _check(lib().mm_batch_create(ctypes.byref(out), n, g, c, _darr(Ms), _darr(A), _darr(Ku), _darr(alpha),
+                                 _darr(gamma), _vp(_stream_handle(stream))))
+    return Batch(out, grids)
+
+
+def mm_batch_destroy(b):
+    h, b.handle = b.handle, None
+    if h:
+        _check(lib().mm_batch_destroy(h))
+
+
+def mm_batch_set_field(b, H):
+    _check(lib().mm_batch_set_field(b.handle, _darr([v for h in H for v in h])))
+
+
+def mm_batch_set_m(b, M):
+    _check(lib().mm_batch_set_m(b.handle, _vp(_ptr(M, b.total))))
+
+
+def mm_batch_get_m(b, out):
+    _check(lib().mm_batch_get_m(b.handle, _vp(_ptr(out, b.total))))
+    return out
+
+
+def mm_batch_step(b, n, dt):
+    _check(lib().mm_batch_step(b.handle, int(n), float(dt)))
+
+
+def mm_batch_sync(b):
+    _check(lib().mm_batch_sync(b.handle))
+
+
+def mm_batch_cells(b):
+    return int(lib().mm_batch_cells(b.handle))
+
+
+def mm_batch_autotune(b, dt):
+    choice = (ctypes.c_int * 3)()
+    ms = (ctypes.c_float * 12)()
+    _check(lib().mm_batch_autotune(b.handle, float(dt), choice, ms))
+    return tuple(choice), list(ms)

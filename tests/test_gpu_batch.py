@@ -1,0 +1,82 @@
+"""Batched stepping of independent samples of uneven size (mm_batch_*):
+each sample must follow its own FP64 oracle trajectory, and equal a
+single-sample context run on the same generic kernels bit for bit."""
+import numpy as np
+import pytest
+
+from oracle import llg as L
+from paper_1406_7459_gb300 import inputs
+from tests._helpers import oracle_spectrum, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _make(samples):
+    from paper_1406_7459_gb300 import mm
+    b = mm.mm_batch_create([s["grid"] for s in samples], [s["cell"] for s in samples],
+                           [s["Ms"] for s in samples], [s["A"] for s in samples], [s["Ku"] for s in samples],
+                           [s["alpha"] for s in samples], [s["gamma"] for s in samples])
+    mm.mm_batch_set_field(b, [s["H_ext"] for s in samples])
+    M = np.concatenate([s["M"].reshape(-1) for s in samples])
+    mm.mm_batch_set_m(b, torch.from_numpy(M).cuda())
+    return b
+
+
+def test_batch_matches_oracle_and_single_contexts(monkeypatch):
+    from paper_1406_7459_gb300 import mm
+    samples = inputs.batch_samples(10, seed=7, nx=(16, 96), ny=(16, 40), nz=(1, 3))
+    b = _make(samples)
+    dt, n = 5e-14, 6
+    mm.mm_batch_step(b, n, dt)
+    out = torch.empty(b.total, device="cuda")
+    mm.mm_batch_get_m(b, out)
+    mm.mm_batch_sync(b)
+    got = out.cpu().numpy()
+    monkeypatch.setenv("MM_NO_FAST", "1")
+    for i, s in enumerate(samples):
+        g = s["grid"]
+        mine = got[b.offsets[i]:b.offsets[i + 1]].reshape(3, g[2], g[1], g[0]).astype(np.float64)
+        Kt, Lp = oracle_spectrum(g, s["cell"])
+        ref = L.run_euler(s["M"].astype(np.float64), n, dt, s["cell"], s["Ms"], s["A"], s["Ku"], s["alpha"],
+                          s["gamma"], s["H_ext"], Kt, Lp)
+        assert rel_l2(mine, ref) < 1e-5, (i, g)
+        ctx = mm.mm_create(g, s["cell"], s["Ms"], s["A"], s["Ku"], s["alpha"], s["gamma"])
+        mm.mm_set_field(ctx, s["H_ext"])
+        mm.mm_set_m(ctx, torch.from_numpy(s["M"].reshape(-1)).cuda())
+        mm.mm_step(ctx, n, dt)
+        one = torch.empty(3 * ctx.N, device="cuda")
+        mm.mm_get_m(ctx, one)
+        mm.mm_sync(ctx)
+        assert np.array_equal(one.cpu().numpy(), got[b.offsets[i]:b.offsets[i + 1]]), (i, g)
+
+
+def test_autotune_keeps_state_and_results():
+    from paper_1406_7459_gb300 import mm
+    samples = inputs.batch_samples(16, seed=9, nx=(16, 128), ny=(16, 48), nz=(1, 2))
+    b = _make(samples)
+    before = torch.empty(b.total, device="cuda")
+    mm.mm_batch_get_m(b, before)
+    choice, ms = mm.mm_batch_autotune(b, 5e-14)
+    after = torch.empty(b.total, device="cuda")
+    mm.mm_batch_get_m(b, after)
+    assert torch.equal(before, after)
+    assert choice[0] in (2, 4, 8) and choice[1] in (2, 4) and choice[2] in (128, 256)
+    assert all(m > 0 for m in ms)
+    mm.mm_batch_step(b, 3, 5e-14)
+    mm.mm_batch_get_m(b, after)
+    mm.mm_batch_sync(b)
+    got = after.cpu().numpy()
+    for i, s in enumerate(samples[:4]):
+        g = s["grid"]
+        Kt, Lp = oracle_spectrum(g, s["cell"])
+        ref = L.run_euler(s["M"].astype(np.float64), 3, 5e-14, s["cell"], s["Ms"], s["A"], s["Ku"], s["alpha"],
+                          s["gamma"], s["H_ext"], Kt, Lp)
+        mine = got[b.offsets[i]:b.offsets[i + 1]].reshape(3, g[2], g[1], g[0])
+        assert rel_l2(mine, ref) < 1e-5
