@@ -300,7 +300,7 @@ def run_gpu(args, rank, ws):
     dom = max(kbytes, key=lambda k: passes[k])
     achieved = kbytes[dom] / (passes[dom] * 1e-3) / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    prof = os.path.join(ROOT, "profiles", "traffic_256x256x4.txt")
     if os.path.exists(prof):
         try:
             traffic = json.load(open(prof)).get(dom)
