@@ -182,7 +182,7 @@ def oracle_rate(seconds_budget=15.0, max_steps=None):
 def run_reference(args, rank, ws):
     if rank != 0:
         return 0
-    budget = min(120.0, max(10.0, 0.1 * args.steps))
+    budget = args.ref_seconds if args.ref_seconds else min(120.0, max(10.0, 0.1 * args.steps))
     rate, n, el = oracle_rate(seconds_budget=budget, max_steps=args.steps)
     N = GRID[0] * GRID[1] * GRID[2]
     line = {
@@ -456,6 +456,8 @@ def main():
                          "batch: 512 uneven samples batched vs one at a time")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="time budget of the --impl reference oracle run (default 10-120 s by --steps)")
     ap.add_argument("--quick", action="store_true",
                     help="no clock warm-up loop and no CPU baseline (deterministic launch list for ncu)")
     args = ap.parse_args()

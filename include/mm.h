@@ -235,6 +235,41 @@ long long mm_batch_cells(const mm_batch *b);              /* total cells, or -1 
  */
 int mm_batch_autotune(mm_batch *b, double dt, int choice[3], float *ms_out);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the demag field (not in the paper): a Fourier neural
+ * operator that maps a magnetisation increment dM/Ms on an H x W film
+ * (nz = 1) to H_demag(dM)/Ms.  Width C channels, `modes` retained modes per
+ * axis direction (kx < modes, ky < modes or ky >= H - modes), `layers`
+ * Fourier layers with GELU between them; BF16 weights and activations with
+ * FP32 accumulation (tensor-core mma for the dense contractions), an FP32
+ * master copy of the parameters and Adam.  Parameter vector layout:
+ * [P (C*3), p (C), R_re (L*C*C*2m*m), R_im (same), W (L*C*C), b (L*C),
+ *  Q (3*C), q (3)].  x, y, t are (batch, 3, H, W) FP32 device arrays.
+ * ------------------------------------------------------------------------ */
+typedef struct mm_fno mm_fno;
+int mm_fno_create(mm_fno **out, int H, int W, int width, int modes, int layers, int max_batch,
+                  unsigned long long seed, void *cuda_stream);
+int mm_fno_destroy(mm_fno *f);                                   /* NULL-safe */
+long long mm_fno_param_count(const mm_fno *f);
+int mm_fno_set_params(mm_fno *f, const float *p);                /* host or device; resets Adam */
+int mm_fno_get_params(mm_fno *f, float *p);                      /* host or device */
+int mm_fno_forward(mm_fno *f, int batch, const float *x, float *y);
+/* loss = mean (y - t)^2 and its gradient (grad: host or device, may be NULL); synchronises */
+int mm_fno_grad(mm_fno *f, int batch, const float *x, const float *t, double *loss, float *grad);
+/* one Adam step (beta 0.9, 0.999) with learning rate lr; loss may be NULL */
+int mm_fno_train_step(mm_fno *f, int batch, const float *x, const float *t, float lr, double *loss);
+/*
+ * mm_step_surrogate -- n forward-Euler steps where the demag field is the
+ * exact FFT convolution every `refresh` steps and, in between,
+ * H_ref + Ms * FNO((M - M_ref)/Ms) with (M_ref, H_ref) from the last exact
+ * refresh.  At each refresh the surrogate's prediction is compared with the
+ * exact field; once the relative L2 residual exceeds tol the stepper falls
+ * back to the exact field for the remaining steps.  stats (may be NULL):
+ * {surrogate steps, exact steps, largest residual, fell back (0/1)}.
+ * Synchronises at each refresh.
+ */
+int mm_step_surrogate(mm_ctx *ctx, mm_fno *f, int n, double dt, int refresh, double tol, double stats[4]);
+
 /*
  * mm_demag_field_noalloc -- H_demag of M, like mm_demag_field, for callers
  * that cannot allocate device memory: for example a host program that

@@ -123,6 +123,20 @@ size_t split_smem_z(const Geom& g);
 cudaError_t launch_rk_stage(int N, const LlgCoef& cf, float a_next, float b_acc, int kind, const float* Mst,
                             const float* H, const float* Mb, float* acc, float* out, int* flag, cudaStream_t s);
 
+}  // namespace mmk
+struct mm_fno;
+namespace mmk {
+// FNO surrogate (fno.cu): one-sample forward on a stream; grid check.
+int fno_apply(mm_fno* f, const float* x, float* y, cudaStream_t s);
+bool fno_matches(const mm_fno* f, int nx, int ny, int nz);
+
+// Surrogate-assisted stepping (surrogate.cu).
+cudaError_t sur_scaled_diff(const float* a, const float* b, float s, long long n, float* out, cudaStream_t st);
+cudaError_t sur_axpy(const float* base, const float* y, float s, long long n, float* out, cudaStream_t st);
+cudaError_t sur_resid(const float* a, const float* b, long long n, double* out, cudaStream_t st);
+cudaError_t sur_llg(const Geom& g, const LlgCoef& cf, const float* M, const float* Hd, float* out, int* flag,
+                    cudaStream_t st);
+
 // Tensor set-up (tensor_setup.cu).  Writes N (FP64 octant) and/or Kt.
 cudaError_t tensor_octant_fp64(const int grid[3], const double cell[3], double* N_dev, cudaStream_t s);
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,

@@ -60,6 +60,16 @@ _PROTOS = {
     "mm_batch_sync": (_c_int, [_vp]),
     "mm_batch_cells": (ctypes.c_longlong, [_vp]),
     "mm_batch_autotune": (_c_int, [_vp, _c_double, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float)]),
+    "mm_fno_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _c_int, _c_int, _c_int,
+                               ctypes.c_ulonglong, _vp]),
+    "mm_fno_destroy": (_c_int, [_vp]),
+    "mm_fno_param_count": (ctypes.c_longlong, [_vp]),
+    "mm_fno_set_params": (_c_int, [_vp, _vp]),
+    "mm_fno_get_params": (_c_int, [_vp, _vp]),
+    "mm_fno_forward": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "mm_fno_grad": (_c_int, [_vp, _c_int, _vp, _vp, ctypes.POINTER(_c_double), _vp]),
+    "mm_fno_train_step": (_c_int, [_vp, _c_int, _vp, _vp, ctypes.c_float, ctypes.POINTER(_c_double)]),
+    "mm_step_surrogate": (_c_int, [_vp, _vp, _c_int, _c_double, _c_int, _c_double, ctypes.POINTER(_c_double)]),
 }
 
 _lib = None
@@ -305,3 +315,87 @@ def mm_batch_autotune(b, dt):
     ms = (ctypes.c_float * 12)()
     _check(lib().mm_batch_autotune(b.handle, float(dt), choice, ms))
     return tuple(choice), list(ms)
+
+
+class Fno:
+    """Owned handle of an mm_fno."""
+
+    def __init__(self, handle, H, W, width, modes, layers):
+        self.handle = handle
+        self.H, self.W, self.width, self.modes, self.layers = H, W, width, modes, layers
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.mm_fno_destroy(h)
+
+
+def mm_fno_create(H, W, width=32, modes=16, layers=4, max_batch=8, seed=0, stream=None):
+    out = _vp()
+    _check(lib().mm_fno_create(ctypes.byref(out), H, W, width, modes, layers, max_batch, seed,
+                               _vp(_stream_handle(stream))))
+    return Fno(out, H, W, width, modes, layers)
+
+
+def mm_fno_destroy(f):
+    h, f.handle = f.handle, None
+    if h:
+        _check(lib().mm_fno_destroy(h))
+
+
+def mm_fno_param_count(f):
+    return int(lib().mm_fno_param_count(f.handle))
+
+
+def mm_fno_set_params(f, p):
+    _check(lib().mm_fno_set_params(f.handle, _vp(_ptr(p, mm_fno_param_count(f)))))
+
+
+def mm_fno_get_params(f, out=None):
+    if out is None:
+        out = np.zeros(mm_fno_param_count(f), np.float32)
+    _check(lib().mm_fno_get_params(f.handle, _vp(_ptr(out, mm_fno_param_count(f)))))
+    return out
+
+
+def mm_fno_forward(f, x, y):
+    b = x.numel() // (3 * f.H * f.W)
+    _check(lib().mm_fno_forward(f.handle, b, _vp(_ptr(x)), _vp(_ptr(y))))
+    return y
+
+
+def mm_fno_grad(f, x, t, grad=None):
+    b = x.numel() // (3 * f.H * f.W)
+    loss = _c_double()
+    _check(lib().mm_fno_grad(f.handle, b, _vp(_ptr(x)), _vp(_ptr(t)), ctypes.byref(loss),
+                             _vp(_ptr(grad) if grad is not None else None)))
+    return loss.value
+
+
+def mm_fno_train_step(f, x, t, lr):
+    b = x.numel() // (3 * f.H * f.W)
+    loss = _c_double()
+    _check(lib().mm_fno_train_step(f.handle, b, _vp(_ptr(x)), _vp(_ptr(t)), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def mm_step_surrogate(ctx, f, n, dt, refresh=8, tol=1e-3):
+    st = (ctypes.c_double * 4)()
+    _check(lib().mm_step_surrogate(ctx.handle, f.handle, int(n), float(dt), int(refresh), float(tol), st))
+    return {"surrogate_steps": int(st[0]), "exact_steps": int(st[1]), "max_residual": st[2],
+            "fell_back": bool(st[3])}
+
+
+def fno_param_dict(flat, width, modes, layers):
+    """Split the flat parameter vector into named arrays (the layout of
+    include/mm.h), as float64 for comparisons."""
+    C, m, L = width, modes, layers
+    flat = np.asarray(flat, np.float64)
+    shapes = [("P", (C, 3)), ("p", (C,)), ("R_re", (L, C, C, 2 * m, m)), ("R_im", (L, C, C, 2 * m, m)),
+              ("W", (L, C, C)), ("b", (L, C)), ("Q", (3, C)), ("q", (3,))]
+    out, o = {}, 0
+    for name, shp in shapes:
+        n = int(np.prod(shp))
+        out[name] = flat[o:o + n].reshape(shp)
+        o += n
+    return out

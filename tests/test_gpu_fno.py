@@ -1,0 +1,113 @@
+"""The BF16 FNO surrogate (mm_fno_*): forward pass and gradients against the
+FP64 oracle of oracle/fno.py, training on pairs the solver generates, and
+the surrogate-assisted stepper against the plain stepper."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import fno as OF
+from paper_1406_7459_gb300 import inputs
+from tests._helpers import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _mm():
+    from paper_1406_7459_gb300 import mm
+    return mm
+
+
+def test_fno_forward_and_gradients_match_fp64_oracle():
+    mm = _mm()
+    H, W, C, m, L, B = 32, 32, 8, 4, 2, 2
+    f = mm.mm_fno_create(H, W, C, m, L, max_batch=B, seed=5)
+    flat = mm.mm_fno_get_params(f)
+    rng = np.random.default_rng(0)
+    flat[:] = flat + 0.05 * rng.standard_normal(flat.shape).astype(np.float32)   # nonzero biases too
+    mm.mm_fno_set_params(f, flat)
+    params = mm.fno_param_dict(flat, C, m, L)
+    x = rng.standard_normal((B, 3, H, W)).astype(np.float32)
+    t = rng.standard_normal((B, 3, H, W)).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y = torch.empty_like(xd)
+    mm.mm_fno_forward(f, xd, y)
+    yref = OF.forward(params, x.astype(np.float64), m)
+    assert rel_l2(y.cpu().numpy(), yref) < 2e-2
+    g = torch.empty(flat.size, device="cuda")
+    loss = mm.mm_fno_grad(f, xd, td, g)
+    lref, gref = OF.gradients(params, x.astype(np.float64), t.astype(np.float64), m)
+    assert abs(loss - lref) < 2e-2 * lref
+    gd = mm.fno_param_dict(g.cpu().numpy(), C, m, L)
+    for name in gref:
+        assert rel_l2(gd[name], gref[name]) < 5e-2, name
+
+
+def _pairs(grid, cell, n_traj, steps, seed):
+    """(dM/Ms, H_demag(dM)/Ms) from solver trajectories: random starts,
+    alpha 0.02, random fields; increments over 1..8 steps."""
+    mm = _mm()
+    rng = np.random.default_rng(seed)
+    ctx = mm.mm_create(grid, cell, 8.6e5, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
+    N3 = 3 * ctx.N
+    xs, ys = [], []
+    for tr in range(n_traj):
+        d = rng.standard_normal(3)
+        mm.mm_set_field(ctx, tuple(rng.uniform(0, 5e4) * d / np.linalg.norm(d)))
+        mm.mm_set_m(ctx, torch.from_numpy(inputs.perturbed_m(grid, 8.6e5, seed * 1000 + tr, 0.5).reshape(-1)).cuda())
+        states = []
+        buf = torch.empty(N3, device="cuda")
+        for s in range(steps):
+            mm.mm_step(ctx, 1, 5e-14)
+            mm.mm_get_m(ctx, buf)
+            states.append(buf.clone())
+        for s in range(0, steps - 8, 2):
+            k = int(rng.integers(1, 9))
+            dM = (states[s + k] - states[s]).contiguous()
+            h = torch.empty_like(dM)
+            mm.mm_demag_field(ctx, dM, h)
+            xs.append(dM / 8.6e5)
+            ys.append(h / 8.6e5)
+    torch.cuda.synchronize()
+    return torch.stack(xs), torch.stack(ys)
+
+
+def test_surrogate_trains_and_steps_within_tolerance():
+    mm = _mm()
+    grid, cell = (64, 64, 1), (5e-9, 5e-9, 3e-9)
+    X, Y = _pairs(grid, cell, n_traj=6, steps=60, seed=1)
+    f = mm.mm_fno_create(64, 64, width=16, modes=8, layers=2, max_batch=8, seed=3)
+    B = 8
+    rng = np.random.default_rng(2)
+    first = None
+    for it in range(400):
+        idx = torch.from_numpy(rng.integers(0, X.shape[0], B)).cuda()
+        loss = mm.mm_fno_train_step(f, X[idx].contiguous(), Y[idx].contiguous(), 3e-3 if it < 300 else 1e-3)
+        first = loss if first is None else first
+    assert loss < 0.05 * first, (first, loss)
+    # surrogate-assisted steps against plain steps from the same state
+    ctx_a = mm.mm_create(grid, cell, 8.6e5, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
+    ctx_b = mm.mm_create(grid, cell, 8.6e5, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
+    M0 = torch.from_numpy(inputs.perturbed_m(grid, 8.6e5, 99, 0.5).reshape(-1)).cuda()
+    for c in (ctx_a, ctx_b):
+        mm.mm_set_field(c, (2e4, 1e4, 0.0))
+        mm.mm_set_m(c, M0)
+    stats = mm.mm_step_surrogate(ctx_a, f, 64, 5e-14, refresh=8, tol=1e-3)
+    mm.mm_step(ctx_b, 64, 5e-14)
+    a, b = torch.empty_like(M0), torch.empty_like(M0)
+    mm.mm_get_m(ctx_a, a)
+    mm.mm_get_m(ctx_b, b)
+    mm.mm_sync(ctx_a)
+    mm.mm_sync(ctx_b)
+    err = rel_l2(a.cpu().numpy() - M0.cpu().numpy(), b.cpu().numpy() - M0.cpu().numpy())
+    print("surrogate: %s, trajectory change error %.3e" % (stats, err))
+    assert stats["exact_steps"] + stats["surrogate_steps"] == 64
+    assert stats["max_residual"] < 1e-3 or stats["fell_back"]
+    assert err < 1e-2
