@@ -243,7 +243,7 @@ int mm_batch_autotune(mm_batch *b, double dt, int choice[3], float *ms_out);
  * Fourier layers with GELU between them; BF16 weights and activations with
  * FP32 accumulation (tensor-core mma for the dense contractions), an FP32
  * master copy of the parameters and Adam.  Parameter vector layout:
- * [P (C*3), p (C), R_re (L*C*C*2m*m), R_im (same), W (L*C*C), b (L*C),
+ * [P (C*5: three inputs, row/H, column/W), p (C), R_re (L*C*C*2m*m), R_im (same), W (L*C*C), b (L*C),
  *  Q (3*C), q (3)].  x, y, t are (batch, 3, H, W) FP32 device arrays.
  * ------------------------------------------------------------------------ */
 typedef struct mm_fno mm_fno;

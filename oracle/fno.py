@@ -6,7 +6,8 @@ field, H_demag(dM)/Ms from dM/Ms on an H x W film (nz = 1), so that between
 exact FFT refreshes H_demag(M) = H_demag(M_ref) + FNO(M - M_ref) (H_demag is
 linear in M).  Architecture (Li et al., Fourier neural operator):
 
-  v0 = P x + p                                   lift, 3 -> C channels
+  v0 = P [x; y/H; x/W] + p                       lift, 3 + 2 coordinate
+                                                 channels -> C channels
   for l < L:  u = W_l v + b_l + S_l(v);  v = gelu(u) (identity for l = L-1)
   y  = Q v + q                                   projection, C -> 3
 
@@ -19,7 +20,9 @@ with the retained modes K = {0..m-1} U {H-m..H-1} (2m rows) and kx < m
 (a_0 = 1, a_kx = 2 otherwise: the real output keeps each kx > 0 and its
 conjugate).  gelu(u) = u (1 + erf(u / sqrt 2)) / 2.  Loss: mean of (y - t)^2.
 
-Parameters are a dict of float64 arrays: P (C,3), p (C), R_re / R_im
+The two coordinate channels (row index / H, column index / W) let the
+operator see the film's edges (the spectral part alone is periodic).
+Parameters are a dict of float64 arrays: P (C,5), p (C), R_re / R_im
 (L, C, C, 2m, m), W (L, C, C) [out, in], b (L, C), Q (3, C), q (3).
 """
 import numpy as np
@@ -32,7 +35,7 @@ def init_params(C, m, L, seed, scale=1.0):
     rng = np.random.default_rng(seed)
     s = scale
     return {
-        "P": rng.standard_normal((C, 3)) * s / np.sqrt(3.0),
+        "P": rng.standard_normal((C, 5)) * s / np.sqrt(5.0),
         "p": np.zeros(C),
         "R_re": rng.standard_normal((L, C, C, 2 * m, m)) * s / C,
         "R_im": rng.standard_normal((L, C, C, 2 * m, m)) * s / C,
@@ -77,13 +80,20 @@ def gelu_grad(u):
     return 0.5 * (1.0 + erf(u / SQRT2)) + u * np.exp(-0.5 * u * u) / np.sqrt(2.0 * np.pi)
 
 
+def with_coords(xb):
+    """(3, H, W) -> (5, H, W): the input plus row / H and column / W."""
+    _, H, W = xb.shape
+    yy, xx = np.meshgrid(np.arange(H) / H, np.arange(W) / W, indexing="ij")
+    return np.concatenate([xb, yy[None], xx[None]])
+
+
 def forward(params, x, m, keep=False):
     """x: (B, 3, H, W) -> y (B, 3, H, W); with keep, the intermediates."""
     L = params["W"].shape[0]
     R = params["R_re"] + 1j * params["R_im"]
     ys, caches = [], []
     for xb in x:
-        v = np.einsum("oc,chw->ohw", params["P"], xb) + params["p"][:, None, None]
+        v = np.einsum("oc,chw->ohw", params["P"], with_coords(xb)) + params["p"][:, None, None]
         cache = {"v": [v], "u": [], "vh": []}
         for l in range(L):
             s, vh = spectral(v, R[l], m)
@@ -134,7 +144,7 @@ def gradients(params, x, t, m):
             full = np.zeros((dvh.shape[0], H, W), complex)
             full[:, kys, :m] = dvh
             dv = dv + (H * W) * np.real(np.fft.ifft2(full))
-        g["P"] += np.einsum("ohw,chw->oc", dv, x[bi])
+        g["P"] += np.einsum("ohw,chw->oc", dv, with_coords(x[bi]))
         g["p"] += dv.sum(axis=(1, 2))
     g["R_re"] = dR.real
     g["R_im"] = dR.imag

@@ -4,7 +4,8 @@
 // Not in the paper.  The network maps a magnetisation increment dM/Ms on an
 // H x W film to its demag field H_demag(dM)/Ms (H_demag is linear in M, so
 // between exact refreshes H_demag(M) = H_demag(M_ref) + Ms FNO((M-M_ref)/Ms)).
-//   v0 = P x + p;  for l < L: u = W_l v + b_l + S_l(v), v = gelu(u) (not on
+//   v0 = P [x; y/H; x/W] + p (two coordinate channels let the operator see
+//   the film's edges);  for l < L: u = W_l v + b_l + S_l(v), v = gelu(u) (not on
 //   the last layer);  y = Q v + q;  S_l keeps kx < m and ky in
 //   {0..m-1} U {H-m..H-1}, with complex weights R_l[c][o] per mode.
 // Dense contractions (the x-direction mode transforms, the channel mixes)
@@ -252,6 +253,40 @@ __global__ void k_dR(const float* __restrict__ dwr, const float* __restrict__ dw
     }
 }
 
+// lift: out[b][o][p] = sum_{c<3} P[o][c] x[b][c][p] + P[o][3] y/H + P[o][4] x/W + bias[o]
+__global__ void k_lift(const float* __restrict__ in, const float* __restrict__ P, const float* __restrict__ bias,
+                       int C, int H, int W, int B, float* __restrict__ out) {
+    const long long np = (long long)H * W, total = (long long)B * np;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(t / np);
+        const long long p = t - (long long)b * np;
+        const float x0 = in[((long long)b * 3 + 0) * np + p], x1 = in[((long long)b * 3 + 1) * np + p];
+        const float x2 = in[((long long)b * 3 + 2) * np + p];
+        const float cy = (float)(p / W) / (float)H, cx = (float)(p % W) / (float)W;
+        for (int o = 0; o < C; ++o)
+            out[((long long)b * C + o) * np + p] =
+                bias[o] + P[o * 5] * x0 + P[o * 5 + 1] * x1 + P[o * 5 + 2] * x2 + P[o * 5 + 3] * cy + P[o * 5 + 4] * cx;
+    }
+}
+
+// g[o][c] += sum_p dv[b][o][p] * feature_c(p), features 3 and 4 the coordinates
+__global__ void k_outer_lift(const float* __restrict__ a, int C, const float* __restrict__ x, int H, int W, int B,
+                             float* __restrict__ g) {
+    const int o = blockIdx.y / 5, c = blockIdx.y % 5;
+    const long long np = (long long)H * W;
+    float acc = 0.f;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)B * np;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(t / np);
+        const long long p = t - (long long)b * np;
+        const float f = c < 3 ? x[((long long)b * 3 + c) * np + p]
+                              : (c == 3 ? (float)(p / W) / (float)H : (float)(p % W) / (float)W);
+        acc += a[((long long)b * C + o) * np + p] * f;
+    }
+    for (int q = 16; q > 0; q >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, q);
+    if ((threadIdx.x & 31) == 0) atomicAdd(g + o * 5 + c, acc);
+}
+
 // u[b][o][p] += bias[o]
 __global__ void k_add_bias(float* __restrict__ u, const float* __restrict__ bias, int C, long long np, int B) {
     const long long n = (long long)B * C * np;
@@ -341,7 +376,7 @@ struct mm_fno {
     long long np;                 // pixels per channel
     cudaStream_t s;
     // parameters: FP32 master, gradient, Adam moments; layout
-    // [P (C*3), p (C), R_re (L*C*C*2m*m), R_im, W (L*C*C), b (L*C), Q (3*C), q (3)]
+    // [P (C*5), p (C), R_re (L*C*C*2m*m), R_im, W (L*C*C), b (L*C), Q (3*C), q (3)]
     long long n_params;
     long long oP, op, oRr, oRi, oW, ob, oQ, oq;
     float *w = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
@@ -421,7 +456,7 @@ extern "C" int mm_fno_create(mm_fno** out, int H, int W, int width, int modes, i
     f->s = (cudaStream_t)stream;
     const int C = width, m = modes, L = layers;
     const long long nR = (long long)L * C * C * 2 * m * m;
-    f->oP = 0; f->op = 3LL * C; f->oRr = f->op + C; f->oRi = f->oRr + nR; f->oW = f->oRi + nR;
+    f->oP = 0; f->op = 5LL * C; f->oRr = f->op + C; f->oRi = f->oRr + nR; f->oW = f->oRi + nR;
     f->ob = f->oW + (long long)L * C * C; f->oQ = f->ob + (long long)L * C; f->oq = f->oQ + 3LL * C;
     f->n_params = f->oq + 3;
     int rc = [&]() -> int {
@@ -430,11 +465,11 @@ extern "C" int mm_fno_create(mm_fno** out, int H, int W, int width, int modes, i
         FCU(cudaMalloc(&f->m1, 4 * n)); FCU(cudaMalloc(&f->m2, 4 * n));
         FCU(cudaMemset(f->m1, 0, 4 * n)); FCU(cudaMemset(f->m2, 0, 4 * n));
         FCU(cudaMalloc(&f->wb, 2LL * L * C * C));
-        // seeded initial weights (scale as in the FP64 reference): P ~ N/sqrt3,
+        // seeded initial weights (scale as in the FP64 reference): P ~ N/sqrt5,
         // R ~ N/C, W ~ N/sqrt C, Q ~ N/sqrt C, biases 0
         std::vector<float> h(n, 0.f);
         uint64_t st = seed;
-        for (long long i = 0; i < 3LL * C; ++i) h[f->oP + i] = (float)(gauss(st) / std::sqrt(3.0));
+        for (long long i = 0; i < 5LL * C; ++i) h[f->oP + i] = (float)(gauss(st) / std::sqrt(5.0));
         for (long long i = 0; i < 2 * nR; ++i) h[f->oRr + i] = (float)(gauss(st) / C);
         for (long long i = 0; i < (long long)L * C * C; ++i) h[f->oW + i] = (float)(gauss(st) / std::sqrt((double)C));
         for (long long i = 0; i < 3LL * C; ++i) h[f->oQ + i] = (float)(gauss(st) / std::sqrt((double)C));
@@ -535,7 +570,7 @@ static int fno_forward(mm_fno* f, int B, const float* x) {
     const long long np = f->np, act = (long long)B * C * np;
     cudaStream_t s = f->s;
     k_to_bf16<<<grid1((long long)L * C * C), 256, 0, s>>>(f->w + f->oW, f->wb, (long long)L * C * C, 1.f);
-    k_pointwise<<<grid1(B * np), 256, 0, s>>>(x, 3, f->w + f->oP, f->w + f->op, C, np, B, 0, f->vf[0]);
+    k_lift<<<grid1(B * np), 256, 0, s>>>(x, f->w + f->oP, f->w + f->op, C, H, W, B, f->vf[0]);
     k_to_bf16<<<grid1(act), 256, 0, s>>>(f->vf[0], f->vb[0], act, 1.f);
     const int nmode = 2 * m * m;
     for (int l = 0; l < L; ++l) {
@@ -630,7 +665,7 @@ static int fno_backward(mm_fno* f, int B, const float* x, const float* t) {
         f->dv = f->tmp;
         f->tmp = t2;
     }
-    k_outer<<<dim3(gx, C * 3), 256, 0, s>>>(f->dv, C, x, 3, np, B, f->g + f->oP);
+    k_outer_lift<<<dim3(gx, C * 5), 256, 0, s>>>(f->dv, C, x, H, W, B, f->g + f->oP);
     k_colsum<<<dim3(gx, C), 256, 0, s>>>(f->dv, C, np, B, f->g + f->op);
     FCU(cudaGetLastError());
     return MM_OK;

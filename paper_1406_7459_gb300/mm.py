@@ -391,7 +391,7 @@ def fno_param_dict(flat, width, modes, layers):
     include/mm.h), as float64 for comparisons."""
     C, m, L = width, modes, layers
     flat = np.asarray(flat, np.float64)
-    shapes = [("P", (C, 3)), ("p", (C,)), ("R_re", (L, C, C, 2 * m, m)), ("R_im", (L, C, C, 2 * m, m)),
+    shapes = [("P", (C, 5)), ("p", (C,)), ("R_re", (L, C, C, 2 * m, m)), ("R_im", (L, C, C, 2 * m, m)),
               ("W", (L, C, C)), ("b", (L, C)), ("Q", (3, C)), ("q", (3,))]
     out, o = {}, 0
     for name, shp in shapes:

@@ -61,7 +61,8 @@ def _pairs(grid, cell, n_traj, steps, seed):
     for tr in range(n_traj):
         d = rng.standard_normal(3)
         mm.mm_set_field(ctx, tuple(rng.uniform(0, 5e4) * d / np.linalg.norm(d)))
-        mm.mm_set_m(ctx, torch.from_numpy(inputs.perturbed_m(grid, 8.6e5, seed * 1000 + tr, 0.5).reshape(-1)).cuda())
+        mm.mm_set_m(ctx, torch.from_numpy(inputs.perturbed_m(grid, 8.6e5, seed * 1000 + tr, 0.3).reshape(-1)).cuda())
+        mm.mm_step(ctx, 20, 5e-14)
         states = []
         buf = torch.empty(N3, device="cuda")
         for s in range(steps):
@@ -87,18 +88,21 @@ def test_surrogate_trains_and_steps_within_tolerance():
     B = 8
     rng = np.random.default_rng(2)
     first = None
-    for it in range(400):
+    for it in range(800):
         idx = torch.from_numpy(rng.integers(0, X.shape[0], B)).cuda()
-        loss = mm.mm_fno_train_step(f, X[idx].contiguous(), Y[idx].contiguous(), 3e-3 if it < 300 else 1e-3)
+        loss = mm.mm_fno_train_step(f, X[idx].contiguous(), Y[idx].contiguous(), 3e-3 if it < 600 else 1e-3)
         first = loss if first is None else first
     assert loss < 0.05 * first, (first, loss)
     # surrogate-assisted steps against plain steps from the same state
     ctx_a = mm.mm_create(grid, cell, 8.6e5, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
     ctx_b = mm.mm_create(grid, cell, 8.6e5, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
-    M0 = torch.from_numpy(inputs.perturbed_m(grid, 8.6e5, 99, 0.5).reshape(-1)).cuda()
+    M0 = torch.from_numpy(inputs.perturbed_m(grid, 8.6e5, 99, 0.3).reshape(-1)).cuda()
     for c in (ctx_a, ctx_b):
         mm.mm_set_field(c, (2e4, 1e4, 0.0))
         mm.mm_set_m(c, M0)
+        mm.mm_step(c, 20, 5e-14)
+    M0 = torch.empty_like(M0)
+    mm.mm_get_m(ctx_b, M0)
     stats = mm.mm_step_surrogate(ctx_a, f, 64, 5e-14, refresh=8, tol=1e-3)
     mm.mm_step(ctx_b, 64, 5e-14)
     a, b = torch.empty_like(M0), torch.empty_like(M0)
