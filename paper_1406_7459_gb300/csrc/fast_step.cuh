@@ -217,7 +217,7 @@ template <int N, int R> struct XstepLayout {
     static constexpr int L = 2 * N, H = N + 1, NL = 3 * R / 2;
     static constexpr int ZS = 2 * N + 2;                  // forward line stride: [h][m] halves of N
     static constexpr int HM = N / 2 + 1;                  // staged kx per parity: kx = 2 m + parity
-    static constexpr int MROWS = 3 * R + 2;                // rows of the M tile per component
+    static constexpr int MROWS = R;                        // rows of the M tile per component
     static constexpr int TW_OFF = 0;
     static constexpr int MT_OFF = L;                              // float2 units; floats: 3*MROWS*N
     static constexpr int MT_C = 3 * MROWS * N / 2;
@@ -249,31 +249,19 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     const size_t Nc = (size_t)g.N;
     const size_t plane_xy = (size_t)N * g.ny;
 
-    // prologue: twiddles and the M^n tile.  Tile rows per component:
-    // [0, R+2): layer k rows j0-1 .. j0+R (clamped: a missing neighbour
-    // row is the edge row itself, the free-boundary rule of Eq. (4));
-    // [R+2, 2R+2): layer k-1 rows j0..j0+R-1; [2R+2, 3R+2): layer k+1.
+    // prologue: twiddles and the tile's own M^n rows.  The exchange
+    // stencil of Eq. (4) is folded into the 2-D spectrum as the zero-padded
+    // stencil, so no neighbour rows are needed; what remains of the
+    // free-boundary rule is local (see the field loop below).
     for (int i = threadIdx.x; i < L / 2; i += blockDim.x) copy16(tw + 2 * i, g.twx + 2 * i);
     {
         constexpr int CH = N / 4;                               // 16-byte chunks per row
-        const int km = k > 0 ? k - 1 : k, kp = k + 1 < g.nz ? k + 1 : k;
-        for (int idx = threadIdx.x; idx < 3 * Lay::MROWS * CH; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < 3 * R * CH; idx += blockDim.x) {
             const int ch = idx % CH;
-            const int row = (idx / CH) % Lay::MROWS;
-            const int c = idx / (CH * Lay::MROWS);
-            int kk = k, jj;
-            if (row < R + 2) {
-                jj = j0 - 1 + row;
-                jj = jj < 0 ? 0 : (jj >= g.ny ? g.ny - 1 : jj);
-            } else if (row < 2 * R + 2) {
-                kk = km;
-                jj = j0 + row - (R + 2);
-            } else {
-                kk = kp;
-                jj = j0 + row - (2 * R + 2);
-            }
-            copy16(Mt + ((size_t)c * Lay::MROWS + row) * N + 4 * ch,
-                   M + c * Nc + (size_t)kk * plane_xy + (size_t)jj * N + 4 * ch);
+            const int row = (idx / CH) % R;
+            const int c = idx / (CH * R);
+            copy16(Mt + ((size_t)c * R + row) * N + 4 * ch,
+                   M + c * Nc + (size_t)k * plane_xy + (size_t)(j0 + row) * N + 4 * ch);
         }
     }
     __pipeline_commit();
@@ -339,7 +327,11 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         }
     }
     __syncthreads();
-    // ---- field, LLG, Euler, renormalisation per cell; new rows to Mn
+    // ---- field, LLG, Euler, renormalisation per cell; new rows to Mn.
+    // The spectrum carries the zero-padded exchange stencil; a cell on a
+    // free face lacks that neighbour, whose term in Eq. (4) is M(i) itself
+    // (zero change), so each missing neighbour adds pexch M(i) / delta^2.
+    const float bz = cf.pexch * (float)((g.nz > 1) * ((k == 0) + (k == g.nz - 1))) * cf.idz2;
     for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
         const int r = idx / N;
         const int i = idx % N;
@@ -351,20 +343,15 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
             const float2 z = wk[ln * L + i];
             hd[cc] = (r & 1) ? z.y : z.x;
         }
-        const int im = i > 0 ? i - 1 : i, ip = i + 1 < N ? i + 1 : i;
+        const float bnd = bz + cf.pexch * ((float)((i == 0) + (i == N - 1)) * cf.idx2 +
+                                           (float)((g.ny > 1) * ((j == 0) + (j == g.ny - 1))) * cf.idy2);
         float m[3], hh[3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const float* T = Mt + (size_t)cc * Lay::MROWS * N;
-            const float* row = T + (r + 1) * N;
-            const float m0 = row[i];
-            const float lap = (row[ip] - 2.f * m0 + row[im]) * cf.idx2 +
-                              (T[(r + 2) * N + i] - 2.f * m0 + T[r * N + i]) * cf.idy2 +
-                              (T[(2 * R + 2 + r) * N + i] - 2.f * m0 + T[(R + 2 + r) * N + i]) * cf.idz2;
+            const float m0 = Mt[((size_t)cc * R + r) * N + i];
             m[cc] = m0;
-            hh[cc] = hd[cc] + cf.pexch * lap;
+            hh[cc] = hd[cc] + bnd * m0;
         }
-        (void)j;
         hh[0] += cf.hx;
         hh[1] += cf.panis * m[1] + cf.hy;
         hh[2] += cf.panis * m[2] + cf.hz;

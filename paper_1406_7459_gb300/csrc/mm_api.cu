@@ -333,7 +333,17 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         if (e == cudaSuccess) e = cudaMalloc(&w1, sizeof(double) * wn);
         if (e == cudaSuccess) e = cudaMalloc(&w2, sizeof(double) * wn);
         if (e == cudaSuccess) e = tensor_octant_fp64(c->grid, c->cell, Nd, c->stream);
-        if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream, c->Kd);
+        ExchangeFold exf{};
+        exf.on = c->has_fs ? 1 : 0;
+        exf.nx = g.nx;
+        exf.ny = g.ny;
+        exf.Lx = g.Lx;
+        exf.Ly = g.Ly;
+        exf.pexch = 2.0 * c->A / (kMu0 * c->Ms * c->Ms);
+        exf.idx2 = 1.0 / (c->cell[0] * c->cell[0]);
+        exf.idy2 = 1.0 / (c->cell[1] * c->cell[1]);
+        exf.idz2 = 1.0 / (c->cell[2] * c->cell[2]);
+        if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream, c->Kd, exf);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         cudaFree(Nd);
         cudaFree(w1);

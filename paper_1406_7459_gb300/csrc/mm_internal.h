@@ -26,7 +26,8 @@ struct Geom {
     const float2* twy;
     const float2* twz;
     const float* Kt;           // tensor spectrum [kx][kz'][ky'][6], scaled
-    const float* Kd;           // 2-D (x, y) tensor spectrum per z offset [kx][ky'][dz][6], scaled;
+    const float* Kd;           // 2-D (x, y) tensor spectrum per z offset [kx][ky'][dz][6], scaled,
+                               // with the zero-padded exchange stencil folded into xx, yy, zz;
                                // used by the direct-z plane kernel of the power-of-two step
 };
 
@@ -139,8 +140,15 @@ cudaError_t sur_llg(const Geom& g, const LlgCoef& cf, const float* M, const floa
 
 // Tensor set-up (tensor_setup.cu).  Writes N (FP64 octant) and/or Kt.
 cudaError_t tensor_octant_fp64(const int grid[3], const double cell[3], double* N_dev, cudaStream_t s);
+// Exchange stencil folded into the 2-D spectrum of the two-kernel step.
+struct ExchangeFold {
+    int on;
+    int nx, ny, Lx, Ly;
+    double pexch, idx2, idy2, idz2;
+};
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
-                            double* work1, double* work2, cudaStream_t s, float* Kd_dev = nullptr);
+                            double* work1, double* work2, cudaStream_t s, float* Kd_dev = nullptr,
+                            ExchangeFold ex = ExchangeFold{});
 size_t tensor_work_elems(const int grid[3], const int L[3]);
 
 // Energy (energy.cu): E[0..4] into out_dev (5 doubles, device); partials is

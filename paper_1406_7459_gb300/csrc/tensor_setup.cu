@@ -232,8 +232,12 @@ __global__ void k_tz(int nz, int Hx, int Hy, int Lz, int Hz, double scale, const
 // stored d_c = s_c N2_c / (Lx Ly) with s = (-1, +1, +1, -1, +1, -1) for
 // (xx, xy, xz, yy, yz, zz); H_z' takes -d_xz, -d_yz.  Layout
 // Kd[kx][ky][dz][c], dz = 0..nz-1 (negative offsets: xz, yz change sign).
+// With ex.on the exchange operator of Eq. (4) is folded in as the
+// zero-padded 7-point stencil (its free-boundary remainder, M(i) times the
+// number of missing neighbours / delta^2, is added per cell by the update
+// kernel), so that the update needs no neighbour cells.
 __global__ void k_pack2d(int nz, int Hx, int Hy, double scale, const double* __restrict__ in,
-                         float* __restrict__ Kd) {
+                         float* __restrict__ Kd, ExchangeFold ex) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t total = (size_t)6 * Hx * Hy * nz;
     if (t >= total) return;
@@ -243,7 +247,20 @@ __global__ void k_pack2d(int nz, int Hx, int Hy, double scale, const double* __r
     const int kx = (int)(t / ((size_t)6 * nz * Hy));
     const double v = in[(((size_t)c * nz + dz) * Hy + ky) * Hx + kx];
     const double sg = (c == 0 || c == 3 || c == 5) ? -1.0 : 1.0;
-    Kd[t] = (float)(sg * scale * v);
+    double e = 0.0;
+    if (ex.on && (c == 0 || c == 3 || c == 5)) {
+        // zero-padded 7-point stencil of Eq. (4) in the (kx, ky, dz) domain,
+        // axes with a single cell skipped
+        if (dz == 0) {
+            if (ex.nx > 1) e += (2.0 * cospi(2.0 * kx / ex.Lx) - 2.0) * ex.idx2;
+            if (ex.ny > 1) e += (2.0 * cospi(2.0 * ky / ex.Ly) - 2.0) * ex.idy2;
+            if (nz > 1) e -= 2.0 * ex.idz2;
+        } else if (dz == 1) {
+            e += ex.idz2;
+        }
+        e *= ex.pexch;
+    }
+    Kd[t] = (float)(scale * (sg * v + e));
 }
 
 // Roots and weights of the n-point Gauss-Legendre rule on [-1, 1] by Newton
@@ -314,7 +331,7 @@ size_t tensor_work_elems(const int grid[3], const int L[3]) {
 }
 
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
-                            double* work1, double* work2, cudaStream_t s, float* Kd_dev) {
+                            double* work1, double* work2, cudaStream_t s, float* Kd_dev, ExchangeFold ex) {
     const int nx = grid[0], ny = grid[1], nz = grid[2];
     const int Hx = L[0] / 2 + 1, Hy = L[1] / 2 + 1, Hz = L[2] / 2 + 1;
     double2* cs = nullptr;
@@ -331,7 +348,8 @@ cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_d
     k_ty<<<(unsigned)((n2 + T - 1) / T), T, 0, s>>>(ny, nz, Hx, L[1], Hy, work1, work2, csy);
     if (Kd_dev) {
         const size_t nd = (size_t)6 * Hx * Hy * nz;
-        k_pack2d<<<(unsigned)((nd + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, 1.0 / ((double)L[0] * L[1]), work2, Kd_dev);
+        k_pack2d<<<(unsigned)((nd + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, 1.0 / ((double)L[0] * L[1]), work2, Kd_dev,
+                                                            ex);
     }
     size_t n3 = (size_t)6 * Hx * Hy * Hz;
     const double scale = 1.0 / ((double)L[0] * L[1] * L[2]);
