@@ -18,6 +18,7 @@
 // Inverse transforms conjugate in and out.  Twiddles come from a shared
 // table tw[k] = W_L^k, k < L = 2n (so W_n^k = tw[2k]).
 #pragma once
+#include <cuda_pipeline.h>
 #include "fft_device.cuh"
 
 namespace mmk {
@@ -152,6 +153,39 @@ template <int N> struct Fft2 {
         if (conj_out) {
 #pragma unroll
             for (int b = 0; b < Q; ++b) w[b].y = -w[b].y;
+        }
+    }
+
+    // Table-driven variants for kernels that keep, besides tw, the table
+    // ta[a Q + t] = W_N^{t a} (a < P, t < Q) in shared memory: every twiddle
+    // is one conflict-free load (consecutive t read consecutive words).
+    static __device__ __forceinline__ void stepA_tab(float2 (&v)[P], int t, const float2* ta, float2* ex,
+                                                     bool conj_in) {
+        if (conj_in) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) v[p].y = -v[p].y;
+        }
+        dftp<P>(v);
+#pragma unroll
+        for (int a = 1; a < P; ++a) v[a] = cmul(v[a], ta[a * Q + t]);
+        store_ex(v, t, ex);
+    }
+    // x_j *= W_{2N}^j, j = t + Q q
+    static __device__ __forceinline__ void odd_input_tab(float2 (&v)[P], int t, const float2* tw) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) v[q] = cmul(v[q], tw[t + Q * q]);
+    }
+    // y_n *= W_{2N}^{-n}, n = a + P b
+    static __device__ __forceinline__ void odd_output_tab(float2 (&w)[Q], int a, const float2* tw) {
+#pragma unroll
+        for (int b = 0; b < Q; ++b) w[b] = cmul(w[b], cconj(tw[a + P * b]));
+    }
+    // Fill ta from the W_{2N} table in global memory (asynchronous 8-byte
+    // copies; the caller commits and waits with its other prologue copies).
+    static __device__ __forceinline__ void load_ta(float2* ta, const float2* tw_global) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int a = i / Q, t = i - a * Q;
+            __pipeline_memcpy_async(ta + i, tw_global + 2 * t * a, sizeof(float2));
         }
     }
 

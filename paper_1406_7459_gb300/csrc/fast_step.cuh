@@ -35,18 +35,24 @@ __device__ __forceinline__ void copy16(void* dst, const void* src) { __pipeline_
 
 template <int a, int b> struct cmax { static constexpr int v = a > b ? a : b; };
 
+// Rows of one x-step tile (row pairs pack two real rows into one complex
+// transform).  Both kernels keep the spectrum as [kx][c][k][j]: a plane
+// reads and writes whole lines, an x-step tile gathers R-row runs.
+constexpr int kStepRows = 2;
+
 // ------------------------------------------------------------- K_A plane --
 template <int NY, int NZ> struct PlaneLayout {
     using F = Fft2<NY>;
     static constexpr int LY = 2 * NY, NL = 3 * NZ;
     static constexpr int ZS = 2 * NY + 2;                 // line stride: [h][m], two halves of NY
     static constexpr int HY = NY + 1;
-    static constexpr int KT_FLOATS = HY * NZ * 6;         // one kx slice of the 2-D spectrum
-    // held in shared memory transposed, [dz*6 + c][ky], so that consecutive
-    // threads (consecutive ky) read consecutive words
-    static constexpr int KT_C = (KT_FLOATS + 1) / 2;      // in float2 units
+    static constexpr int HYP = kd_row(HY);                // row of the 2-D spectrum, 16-byte multiple
+    static constexpr int KT_FLOATS = HYP * NZ * 6;        // one kx slice of the 2-D spectrum,
+    // [dz*6 + c][ky] as stored, so that consecutive threads (consecutive ky)
+    // read consecutive words
+    static constexpr int KT_C = KT_FLOATS / 2;            // in float2 units
     static constexpr int WORK = cmax<NL * ZS, 2 * NL * F::EX>::v;
-    static constexpr int TW_OFF = 0, KT_OFF = LY, WORK_OFF = LY + ((KT_C + 1) / 2) * 2;
+    static constexpr int TW_OFF = 0, TA_OFF = LY, KT_OFF = LY + NY, WORK_OFF = KT_OFF + ((KT_C + 1) / 2) * 2;
     static constexpr size_t BYTES = sizeof(float2) * (WORK_OFF + WORK);
     static constexpr int THREADS = 2 * NL * F::G;
     static constexpr int ZTASKS = 3 * LY;                 // (ky column, output component)
@@ -59,15 +65,15 @@ template <int NY, int NZ> struct PlaneLayout {
 // D(dz) from the stored d(|dz|) = (xx, xy, xz, yy, yz, zz): row x uses
 // (xx, xy, xz), row y (xy, yy, yz), row z' (-xz, -yz, zz); xz and yz change
 // sign for dz < 0 (odd in z) and xy, yz for a mirrored ky (odd in y).
-template <int NZ, int HY>
-__device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], const float* __restrict__ d, int a, float sy,
+template <int NZ>
+__device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], const float (&d)[NZ][6], int a,
                                              float2 (&h)[NZ]) {
 #pragma unroll
     for (int k = 0; k < NZ; ++k) h[k] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int dz = 0; dz < NZ; ++dz) {
-        const float xx = d[(dz * 6 + 0) * HY], xy = sy * d[(dz * 6 + 1) * HY], xz = d[(dz * 6 + 2) * HY];
-        const float yy = d[(dz * 6 + 3) * HY], yz = sy * d[(dz * 6 + 4) * HY], zz = d[(dz * 6 + 5) * HY];
+        const float xx = d[dz][0], xy = d[dz][1], xz = d[dz][2];
+        const float yy = d[dz][3], yz = d[dz][4], zz = d[dz][5];
         float cb0, cb1, cb2;                              // D_a,b for b = x, y, z' at +dz
         float ob0, ob1, ob2;                              // sign-adjusted for -dz
         if (a == 0) { cb0 = xx; cb1 = xy; cb2 = xz; ob0 = xx; ob1 = xy; ob2 = -xz; }
@@ -95,34 +101,33 @@ __device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], const flo
 
 template <int NY, int NZ>
 __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY, NZ>::THREADS <= 512) ? 2 : 1)
-    k_plane_pdl(Geom g, float2* __restrict__ S) {
+    k_plane_pdl(Geom g, const float2* __restrict__ S, float2* __restrict__ Sh) {
     using Lay = PlaneLayout<NY, NZ>;
     using F = Fft2<NY>;
     constexpr int P = F::P, Q = F::Q, G = F::G, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm + Lay::TW_OFF;
+    float2* ta = sm + Lay::TA_OFF;
     float* Ks = reinterpret_cast<float*>(sm + Lay::KT_OFF);
     float2* zb = sm + Lay::WORK_OFF;
     float2* ex = zb;                                      // aliases zb (barriers separate uses)
     const int kx = blockIdx.x;
 
-    // prologue: constant data only
+    // prologue: constant data only (twiddles, this kx's slice of the 2-D
+    // spectrum), asynchronous, so that it overlaps the wait and the S load
     for (int i = threadIdx.x; i < LY / 2; i += blockDim.x) copy16(tw + 2 * i, g.twy + 2 * i);
-    const float* Kp = g.Kd + (size_t)kx * Lay::KT_FLOATS;
-    // copy the slice through registers, transposing [ky][dz*6 + c] -> [dz*6 + c][ky]
-    for (int ky = threadIdx.x; ky < Lay::HY; ky += blockDim.x) {
-        const float2* src = reinterpret_cast<const float2*>(Kp + (size_t)ky * NZ * 6);
-#pragma unroll
-        for (int q = 0; q < NZ * 3; ++q) {
-            const float2 v2 = __ldg(src + q);
-            Ks[(2 * q) * Lay::HY + ky] = v2.x;
-            Ks[(2 * q + 1) * Lay::HY + ky] = v2.y;
-        }
+    F::load_ta(ta, g.twy);
+    {
+        const float* Kp = g.Kd + (size_t)kx * Lay::KT_FLOATS;
+        for (int i = threadIdx.x; i < Lay::KT_FLOATS / 4; i += blockDim.x) copy16(Ks + 4 * i, Kp + 4 * i);
     }
     __pipeline_commit();
     pdl_wait();
+    // S of the previous x-step is complete: the next kernel may launch and
+    // run its prologue (it reads nothing this kernel writes before its own wait)
+    pdl_trigger();
 
-    float2* plane = S + (size_t)kx * NL * g.Jst;
+    const float2* plane = S + (size_t)kx * NL * g.Jst;
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
     const int line = grp >> 1, h = grp & 1;
     float2 v[P];
@@ -135,8 +140,8 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     __syncthreads();
     // forward y (pruned input): odd half pre-multiplied by W_LY^j
     if (t < Q) {
-        if (h) F::odd_input(v, t, tw);
-        F::stepA(v, t, tw, ex + grp * F::EX, false);
+        if (h) F::odd_input_tab(v, t, tw);
+        F::stepA_tab(v, t, ta, ex + grp * F::EX, false);
     }
     __syncthreads();
     float2 w[Q];
@@ -163,10 +168,21 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         int kyp = ky;
         float sy = 1.f;
         if (2 * ky > LY) { kyp = LY - ky; sy = -1.f; }
+        // the column's couplings, read once for the three output components
+        float d[NZ][6];
+#pragma unroll
+        for (int dz = 0; dz < NZ; ++dz)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) d[dz][c] = Ks[(dz * 6 + c) * Lay::HYP + kyp];
+#pragma unroll
+        for (int dz = 0; dz < NZ; ++dz) {
+            d[dz][1] *= sy;
+            d[dz][4] *= sy;
+        }
         float2 hres[NZ];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            zdirect_task<NZ, Lay::HY>(m, Ks + kyp, a, sy, hres);
+            zdirect_task<NZ>(m, d, a, hres);
 #pragma unroll
             for (int k = 0; k < NZ; ++k) {
                 const float2 o = (a == 2) ? make_float2(hres[k].y, -hres[k].x) : hres[k];   // -i H_z'
@@ -181,21 +197,23 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         for (int q = 0; q < P; ++q) v[q] = zb[line * ZS + h * NY + t + Q * q];
     }
     __syncthreads();
-    if (t < Q) F::stepA(v, t, tw, ex + grp * F::EX, true);
+    if (t < Q) F::stepA_tab(v, t, ta, ex + grp * F::EX, true);
     __syncthreads();
     if (t < P) {
         F::stepB(w, t, ex + grp * F::EX, true);
-        if (h) F::odd_output(w, t, tw);
+        if (h) F::odd_output_tab(w, t, tw);
     }
+    float2* outp = Sh + (size_t)kx * NL * g.Jst;
     if constexpr (G == 16) {
         // the two halves of a line are lanes t and t + 16 of one warp
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const float ox = __shfl_down_sync(0xffffffffu, w[q].x, 16);
             const float oy = __shfl_down_sync(0xffffffffu, w[q].y, 16);
-            if (h == 0) plane[(size_t)line * g.Jst + t + P * q] = make_float2(w[q].x + ox, w[q].y + oy);
+            if (h == 0) outp[(size_t)line * g.Jst + t + P * q] = make_float2(w[q].x + ox, w[q].y + oy);
         }
     } else {
+        // zb aliases the exchange buffers that step B has just read
         __syncthreads();
         if (t < P) {
 #pragma unroll
@@ -204,11 +222,9 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         __syncthreads();
         for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
             const int l = idx / NY, n = idx % NY;
-            plane[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + NY + n]);
+            outp[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + NY + n]);
         }
     }
-    __syncthreads();
-    pdl_trigger();
 }
 
 // ------------------------------------------------------------- K_B xstep --
@@ -218,8 +234,8 @@ template <int N, int R> struct XstepLayout {
     static constexpr int ZS = 2 * N + 2;                  // forward line stride: [h][m] halves of N
     static constexpr int HM = N / 2 + 1;                  // staged kx per parity: kx = 2 m + parity
     static constexpr int MROWS = R;                        // rows of the M tile per component
-    static constexpr int TW_OFF = 0;
-    static constexpr int MT_OFF = L;                              // float2 units; floats: 3*MROWS*N
+    static constexpr int TW_OFF = 0, TA_OFF = L;
+    static constexpr int MT_OFF = L + N;                          // float2 units; floats: 3*MROWS*N
     static constexpr int MT_C = 3 * MROWS * N / 2;
     static constexpr int SB_OFF = MT_OFF + MT_C;                  // staged spectrum / new M rows
     static constexpr int SB_C = cmax<3 * H * R, 3 * R * N / 2>::v;
@@ -231,13 +247,15 @@ template <int N, int R> struct XstepLayout {
 
 template <int N, int R>
 __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
-    k_xstep_pdl(Geom g, LlgCoef cf, const float2* __restrict__ S, float2* __restrict__ Snext,
+    k_xstep_pdl(Geom g, LlgCoef cf, const float2* __restrict__ Sh, float2* __restrict__ Snext,
                 const float* __restrict__ M, float* __restrict__ Mout, int* __restrict__ flag) {
+    static_assert(R == kStepRows, "tile rows match the plane kernel's output layout");
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm + Lay::TW_OFF;
+    float2* ta = sm + Lay::TA_OFF;
     float* Mt = reinterpret_cast<float*>(sm + Lay::MT_OFF);
     float2* sb = sm + Lay::SB_OFF;
     float* Mn = reinterpret_cast<float*>(sm + Lay::SB_OFF);     // new M rows, after sb is consumed
@@ -254,6 +272,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     // stencil, so no neighbour rows are needed; what remains of the
     // free-boundary rule is local (see the field loop below).
     for (int i = threadIdx.x; i < L / 2; i += blockDim.x) copy16(tw + 2 * i, g.twx + 2 * i);
+    F::load_ta(ta, g.twx);
     {
         constexpr int CH = N / 4;                               // 16-byte chunks per row
         for (int idx = threadIdx.x; idx < 3 * R * CH; idx += blockDim.x) {
@@ -266,15 +285,12 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     }
     __pipeline_commit();
     pdl_wait();
-    // staged half-spectrum of the H tile: sb[(c*H + kx)*R + r] (R = 2:
-    // one 16-byte copy per (kx, c))
-    for (int kx = threadIdx.x; kx < H; kx += blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float2* src = S + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0;
-#pragma unroll
-            for (int q = 0; q < R / 2; ++q) copy16(sb + (size_t)(c * H + kx) * R + 2 * q, src + 2 * q);
-        }
+    // staged half-spectrum of the H tile: sb[(c*H + kx)*R + r], R-row runs
+    // of the plane kernel's output
+    for (int idx = threadIdx.x; idx < 3 * H * (R / 2); idx += blockDim.x) {
+        const int q = idx % (R / 2), ck = idx / (R / 2);
+        const int c = ck % 3, kx = ck / 3;
+        copy16(sb + (size_t)(c * H + kx) * R + 2 * q, Sh + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * q);
     }
     __pipeline_commit();
     __pipeline_wait_prior(0);
@@ -298,12 +314,12 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
             if (ks == 0 || ks == N) { A.y = 0.f; B.y = 0.f; }
             v[q] = low ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
         }
-        F::stepA(v, t, tw, wk + grp * F::EX, true);
+        F::stepA_tab(v, t, ta, wk + grp * F::EX, true);
     }
     __syncthreads();
     if (fft_thread && t < P) {
         F::stepB(w, t, wk + grp * F::EX, true);
-        if (h) F::odd_output(w, t, tw);
+        if (h) F::odd_output_tab(w, t, tw);
     }
     __syncthreads();
     if constexpr (G == 16) {
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         const float n0 = m[0] + cf.dt * (cf.c1 * p0 + cf.c2 * q0);
         const float n1 = m[1] + cf.dt * (cf.c1 * p1 + cf.c2 * q1);
         const float n2 = m[2] + cf.dt * (cf.c1 * p2 + cf.c2 * q2);
-        const float s = cf.Ms / sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+        const float s = cf.Ms * rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
         const float o0 = n0 * s, o1 = n1 * s, o2 = n2 * s;
         if (!(isfinite(o0) && isfinite(o1) && isfinite(o2))) atomicOr(flag, 1);
         const size_t cell = (size_t)i + (size_t)N * ((size_t)j0 + r) + plane_xy * k;
@@ -385,8 +401,8 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
             const int jx = t + Q * q;
             v[q] = make_float2(ra[jx], rb[jx]);
         }
-        if (h) F::odd_input(v, t, tw);
-        F::stepA(v, t, tw, wk + grp * F::EX, false);
+        if (h) F::odd_input_tab(v, t, tw);
+        F::stepA_tab(v, t, ta, wk + grp * F::EX, false);
     }
     __syncthreads();
     if (fft_thread && t < P) F::stepB(w, t, wk + grp * F::EX, false);

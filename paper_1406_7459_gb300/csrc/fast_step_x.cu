@@ -6,7 +6,7 @@ namespace mmk {
 
 template <int N>
 static void fill_xstep(FastStepFns* f) {
-    constexpr int R = 2;
+    constexpr int R = kStepRows;
     f->kb = k_xstep_pdl<N, R>;
     f->rb = R;
     f->tb = XstepLayout<N, R>::THREADS;
@@ -50,27 +50,28 @@ static cudaLaunchConfig_t step_cfg(dim3 grid, int threads, size_t smem, cudaStre
     return cfg;
 }
 
-cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, float2* S, cudaStream_t s, bool pdl) {
+cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float2* S, float2* Sh, cudaStream_t s,
+                          bool pdl) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = step_cfg(dim3(g.Hx), f.ta, f.sa, s, pdl, attr);
-    return cudaLaunchKernelEx(&cfg, f.ka, g, S);
+    return cudaLaunchKernelEx(&cfg, f.ka, g, S, Sh);
 }
 
-cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* S, float2* Snext,
+cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
                           const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = step_cfg(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, pdl, attr);
-    return cudaLaunchKernelEx(&cfg, f.kb, g, c, S, Snext, M, Mout, flag);
+    return cudaLaunchKernelEx(&cfg, f.kb, g, c, Sh, S, M, Mout, flag);
 }
 
 // K_A then K_B; with `pdl` both carry the programmatic-serialisation launch
 // attribute so each may start while its predecessor drains (each kernel
 // waits on griddepcontrol before reading what the predecessor wrote).
-cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Snext,
+cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
                             const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
-    cudaError_t e = launch_step_a(g, f, S, s, pdl);
+    cudaError_t e = launch_step_a(g, f, S, Sh, s, pdl);
     if (e != cudaSuccess) return e;
-    return launch_step_b(g, f, c, S, Snext, M, Mout, flag, s, pdl);
+    return launch_step_b(g, f, c, Sh, S, M, Mout, flag, s, pdl);
 }
 
 }  // namespace mmk

@@ -54,21 +54,22 @@ struct mm_ctx {
     double* partials = nullptr;
     double* Edev = nullptr;
     float2* tw = nullptr;      // twiddles of x, y, z back to back
-    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
-    double step_dt[2] = {0, 0};
-    unsigned long long step_ver[2] = {0, 0};
+    // step graphs [kind][parity]: kind 0 one step, kind 1 kGraphSteps steps
+    cudaGraphExec_t step_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    double step_dt[2][2] = {{0, 0}, {0, 0}};
+    unsigned long long step_ver[2][2] = {{0, 0}, {0, 0}};
     unsigned long long ver = 1;   // bumped when H_ext changes
     bool use_graphs = true;
     FastFns fast;              // compile-time kernels (when the grid has them)
     FastStepFns fs;            // two-kernel step (power-of-two grids)
     bool has_fs = false;
-    float2* S2 = nullptr;      // second spectrum buffer of the two-kernel step
+    float2* Sh = nullptr;      // plane-kernel output of the two-kernel step (layout of S)
     int method = MM_INTEGRATOR_EULER;
     float* Mst = nullptr;      // Runge-Kutta stage state
     float* acc = nullptr;      // Runge-Kutta weighted slope sum
     float* sur = nullptr;      // surrogate stepper: M_ref, H_ref, x, y, H_d (5 x 3N)
     double* sur_r = nullptr;   // residual sums
-    bool spec_valid = false;   // S[cur] (S or S2) holds the x half-spectrum of M[cur]
+    bool spec_valid = false;   // S holds the x half-spectrum of M[cur] (two-kernel step)
 };
 
 // ------------------------------------------------------------------ plan --
@@ -231,12 +232,13 @@ static LlgCoef make_coef(const mm_ctx* c, double dt) {
 }
 
 static void release(mm_ctx* c) {
-    for (int p = 0; p < 2; ++p)
-        if (c->step_exec[p]) cudaGraphExecDestroy(c->step_exec[p]);
+    for (int kd = 0; kd < 2; ++kd)
+        for (int p = 0; p < 2; ++p)
+            if (c->step_exec[kd][p]) cudaGraphExecDestroy(c->step_exec[kd][p]);
     cudaFree(c->Kt);
     cudaFree(c->Kd);
     cudaFree(c->S);
-    cudaFree(c->S2);
+    cudaFree(c->Sh);
     cudaFree(c->Mbuf[0]);
     cudaFree(c->Mbuf[1]);
     cudaFree(c->H);
@@ -296,8 +298,8 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         CU(cudaMalloc(&c->Kt, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.Hz));
         CU(cudaMalloc(&c->S, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
         if (c->has_fs) {
-            CU(cudaMalloc(&c->S2, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
-            CU(cudaMalloc(&c->Kd, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.nz));
+            CU(cudaMalloc(&c->Sh, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
+            CU(cudaMalloc(&c->Kd, sizeof(float) * 6 * (size_t)g.Hx * kd_row(g.Hy) * g.nz));
         }
         CU(cudaMalloc(&c->Mbuf[0], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->Mbuf[1], sizeof(float) * 3 * N));
@@ -433,8 +435,8 @@ extern "C" int mm_get_m(mm_ctx* c, float* M) {
     return MM_OK;
 }
 
-// The three-pass evaluation on the spectrum workspace S (which is also S[0]
-// of the two-kernel step, so it invalidates a pending spectrum).
+// The three-pass evaluation on the spectrum workspace S (which also holds
+// the two-kernel step's spectrum, so it invalidates a pending one).
 static int run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt, cudaStream_t s) {
     const LlgCoef cf = make_coef(c, dt);
     c->spec_valid = false;
@@ -458,11 +460,9 @@ extern "C" int mm_effective_field(mm_ctx* c, const float* M, float* H) {
     return run_passes(c, kModeHeff, M, H, 0.0, c->stream);
 }
 
-static float2* spec(mm_ctx* c, int p) { return p == 0 ? c->S : c->S2; }
-
-// One step from parity p (M[p] -> M[1-p]).  Two-kernel path: K_A on S[p],
-// K_B into S[1-p], programmatic dependent launch between them.  Generic
-// path: the three passes on S.
+// One step from parity p (M[p] -> M[1-p]).  Two-kernel path: K_A from S
+// into Sh, K_B from Sh into S (the spectrum of M[1-p]), programmatic
+// dependent launch between them.  Generic path: the three passes on S.
 // One explicit Runge-Kutta step (Heun or classic RK4) from parity p: per
 // stage a field evaluation into H, then the stage update.
 static int enqueue_rk_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
@@ -487,21 +487,30 @@ static int enqueue_rk_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
 static int enqueue_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
     if (c->method != MM_INTEGRATOR_EULER) return enqueue_rk_step(c, p, dt, s);
     if (c->has_fs) {
-        CU(launch_step_pdl(c->g, c->fs, make_coef(c, dt), spec(c, p), spec(c, 1 - p), c->Mbuf[p], c->Mbuf[1 - p],
+        CU(launch_step_pdl(c->g, c->fs, make_coef(c, dt), c->S, c->Sh, c->Mbuf[p], c->Mbuf[1 - p],
                            c->flag, s, true));
         return MM_OK;
     }
     return run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, s);
 }
 
-// Capture one step from parity p on the private stream into a graph.
-static int capture_step(mm_ctx* c, int p, double dt) {
-    if (c->step_exec[p]) {
-        cudaGraphExecDestroy(c->step_exec[p]);
-        c->step_exec[p] = nullptr;
+// Steps per multi-step graph (even, so that it ends on the parity it starts
+// from).  Inside one graph consecutive steps keep their programmatic
+// launch edges, so a step's first kernel starts while the previous one drains.
+constexpr int kGraphSteps = 16;
+
+// Capture one step (kind 0) or kGraphSteps steps (kind 1) from parity p on
+// the private stream into a graph.
+static int capture_step(mm_ctx* c, int kind, int p, double dt) {
+    cudaGraphExec_t& ex = c->step_exec[kind][p];
+    if (ex) {
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
     }
     CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_step(c, p, dt, c->cap);
+    int rc = MM_OK;
+    const int ns = kind ? kGraphSteps : 1;
+    for (int s = 0; s < ns && rc == MM_OK; ++s) rc = enqueue_step(c, (p + s) & 1, dt, c->cap);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
     if (rc != MM_OK) {
@@ -509,18 +518,18 @@ static int capture_step(mm_ctx* c, int p, double dt) {
         return rc;
     }
     CU(e);
-    e = cudaGraphInstantiate(&c->step_exec[p], graph, 0);
+    e = cudaGraphInstantiate(&ex, graph, 0);
     cudaGraphDestroy(graph);
     CU(e);
-    c->step_dt[p] = dt;
-    c->step_ver[p] = c->ver;
+    c->step_dt[kind][p] = dt;
+    c->step_ver[kind][p] = c->ver;
     return MM_OK;
 }
 
 // Form S[cur] from M[cur] when the two-kernel step needs it.
 static int ensure_spectrum(mm_ctx* c) {
     if (!c->has_fs || c->spec_valid || c->method != MM_INTEGRATOR_EULER) return MM_OK;
-    CU(launch_pass1(c->g, c->l, c->Mbuf[c->cur], spec(c, c->cur), c->stream));
+    CU(launch_pass1(c->g, c->l, c->Mbuf[c->cur], c->S, c->stream));
     c->spec_valid = true;
     return MM_OK;
 }
@@ -532,19 +541,23 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
     if (n == 0) return MM_OK;
     int rc = ensure_spectrum(c);
     if (rc != MM_OK) return rc;
-    for (int s = 0; s < n; ++s) {
+    for (int s = 0; s < n;) {
         const int p = c->cur;
         if (c->use_graphs) {
-            if (!c->step_exec[p] || c->step_dt[p] != dt || c->step_ver[p] != c->ver) {
-                rc = capture_step(c, p, dt);
+            const int kind = n - s >= kGraphSteps ? 1 : 0;
+            if (!c->step_exec[kind][p] || c->step_dt[kind][p] != dt || c->step_ver[kind][p] != c->ver) {
+                rc = capture_step(c, kind, p, dt);
                 if (rc != MM_OK) return rc;
             }
-            CU(cudaGraphLaunch(c->step_exec[p], c->stream));
+            CU(cudaGraphLaunch(c->step_exec[kind][p], c->stream));
+            if (!kind) c->cur = 1 - p;
+            s += kind ? kGraphSteps : 1;
         } else {
             rc = enqueue_step(c, p, dt, c->stream);
             if (rc != MM_OK) return rc;
+            c->cur = 1 - p;
+            ++s;
         }
-        c->cur = 1 - p;
     }
     return MM_OK;
 }
@@ -626,11 +639,11 @@ extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsig
             CU(cudaEventRecord(ev[0], c->stream));
             if (c->has_fs) {
                 // pass 1 alone (the two-kernel step folds it into K_B), then K_A, K_B
-                CU(launch_pass1(c->g, c->l, c->Mbuf[p], spec(c, p), c->stream));
+                CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
                 CU(cudaEventRecord(ev[1], c->stream));
-                CU(launch_step_a(c->g, c->fs, spec(c, p), c->stream, false));
+                CU(launch_step_a(c->g, c->fs, c->S, c->Sh, c->stream, false));
                 CU(cudaEventRecord(ev[2], c->stream));
-                CU(launch_step_b(c->g, c->fs, cf, spec(c, p), spec(c, 1 - p), c->Mbuf[p], c->Mbuf[1 - p], c->flag,
+                CU(launch_step_b(c->g, c->fs, cf, c->Sh, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag,
                                  c->stream, false));
                 c->spec_valid = true;
             } else {

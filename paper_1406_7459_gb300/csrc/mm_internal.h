@@ -26,10 +26,14 @@ struct Geom {
     const float2* twy;
     const float2* twz;
     const float* Kt;           // tensor spectrum [kx][kz'][ky'][6], scaled
-    const float* Kd;           // 2-D (x, y) tensor spectrum per z offset [kx][ky'][dz][6], scaled,
+    const float* Kd;           // 2-D (x, y) tensor spectrum per z offset [kx][dz][6][ky'], rows of
+                               // kd_row(Hy) floats, scaled,
                                // with the zero-padded exchange stencil folded into xx, yy, zz;
                                // used by the direct-z plane kernel of the power-of-two step
 };
+
+// Row length (floats) of the 2-D spectrum Kd: Hy rounded up to 16 bytes.
+inline __host__ __device__ constexpr int kd_row(int Hy) { return (Hy + 3) & ~3; }
 
 // Field and LLG coefficients in FP32 (computed in FP64 on the host).
 struct LlgCoef {
@@ -96,7 +100,7 @@ bool fast_lookup_plane_nz8(int ny, FastFns* f);
 // Two-kernel step for power-of-two grids (fast_step*.cu): K_A = plane
 // kernel in place on S[p]; K_B = inverse x + LLG + forward x into S[1-p].
 struct FastStepFns {
-    void (*ka)(Geom, float2*) = nullptr;
+    void (*ka)(Geom, const float2*, float2*) = nullptr;
     int ta = 0;
     size_t sa = 0;
     void (*kb)(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*) = nullptr;
@@ -106,11 +110,13 @@ struct FastStepFns {
 bool fast_step_lookup_x(int nx, FastStepFns* f);
 bool fast_step_lookup_plane_a(int ny, int nz, FastStepFns* f);
 bool fast_step_lookup_plane_b(int ny, int nz, FastStepFns* f);
-cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Snext,
+// K_A reads the x half-spectrum S and writes its output to Sh; K_B reads Sh
+// and writes the next step's S.
+cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
                             const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 cudaError_t configure_step_kernels(const FastStepFns& f);
-cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, float2* S, cudaStream_t s, bool pdl);
-cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* S, float2* Snext,
+cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float2* S, float2* Sh, cudaStream_t s, bool pdl);
+cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
                           const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 
 // Pass 2 for thick samples (split_kernels.cu); the spectrum row stride is Ly.

@@ -231,20 +231,27 @@ __global__ void k_tz(int nz, int Hx, int Hy, int Lz, int Hz, double scale, const
 // works with M_z' = i M_z and H_z' = i H_z, which makes every coupling real:
 // stored d_c = s_c N2_c / (Lx Ly) with s = (-1, +1, +1, -1, +1, -1) for
 // (xx, xy, xz, yy, yz, zz); H_z' takes -d_xz, -d_yz.  Layout
-// Kd[kx][ky][dz][c], dz = 0..nz-1 (negative offsets: xz, yz change sign).
+// Kd[kx][dz][c][ky], dz = 0..nz-1 (negative offsets: xz, yz change sign),
+// rows of Hyp = Hy rounded up to 4 floats (zero tail), so that one kx slice
+// is a contiguous run of 16-byte chunks in the order the plane kernel keeps
+// it in shared memory.
 // With ex.on the exchange operator of Eq. (4) is folded in as the
 // zero-padded 7-point stencil (its free-boundary remainder, M(i) times the
 // number of missing neighbours / delta^2, is added per cell by the update
 // kernel), so that the update needs no neighbour cells.
-__global__ void k_pack2d(int nz, int Hx, int Hy, double scale, const double* __restrict__ in,
+__global__ void k_pack2d(int nz, int Hx, int Hy, int Hyp, double scale, const double* __restrict__ in,
                          float* __restrict__ Kd, ExchangeFold ex) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t total = (size_t)6 * Hx * Hy * nz;
+    const size_t total = (size_t)6 * Hx * Hyp * nz;
     if (t >= total) return;
-    const int c = (int)(t % 6);
-    const int dz = (int)((t / 6) % nz);
-    const int ky = (int)((t / ((size_t)6 * nz)) % Hy);
-    const int kx = (int)(t / ((size_t)6 * nz * Hy));
+    const int ky = (int)(t % Hyp);
+    const int c = (int)((t / Hyp) % 6);
+    const int dz = (int)((t / ((size_t)6 * Hyp)) % nz);
+    const int kx = (int)(t / ((size_t)6 * Hyp * nz));
+    if (ky >= Hy) {
+        Kd[t] = 0.f;
+        return;
+    }
     const double v = in[(((size_t)c * nz + dz) * Hy + ky) * Hx + kx];
     const double sg = (c == 0 || c == 3 || c == 5) ? -1.0 : 1.0;
     double e = 0.0;
@@ -347,9 +354,10 @@ cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_d
     size_t n2 = (size_t)6 * nz * Hy * Hx;
     k_ty<<<(unsigned)((n2 + T - 1) / T), T, 0, s>>>(ny, nz, Hx, L[1], Hy, work1, work2, csy);
     if (Kd_dev) {
-        const size_t nd = (size_t)6 * Hx * Hy * nz;
-        k_pack2d<<<(unsigned)((nd + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, 1.0 / ((double)L[0] * L[1]), work2, Kd_dev,
-                                                            ex);
+        const int Hyp = kd_row(Hy);
+        const size_t nd = (size_t)6 * Hx * Hyp * nz;
+        k_pack2d<<<(unsigned)((nd + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, Hyp, 1.0 / ((double)L[0] * L[1]), work2,
+                                                            Kd_dev, ex);
     }
     size_t n3 = (size_t)6 * Hx * Hy * Hz;
     const double scale = 1.0 / ((double)L[0] * L[1] * L[2]);
