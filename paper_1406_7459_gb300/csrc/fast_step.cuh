@@ -229,16 +229,20 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
 
 // ------------------------------------------------------------- K_B xstep --
 template <int N, int R> struct XstepLayout {
+    static_assert(R == 2, "one row pair per tile: the pair shares one complex transform");
     using F = Fft2<N>;
     static constexpr int L = 2 * N, H = N + 1, NL = 3 * R / 2;
-    static constexpr int ZS = 2 * N + 2;                  // forward line stride: [h][m] halves of N
     static constexpr int HM = N / 2 + 1;                  // staged kx per parity: kx = 2 m + parity
+    static constexpr int HP = 2 * HM;                     // staged positions per component
+    static constexpr int HOFF = N + 8;                    // odd-kx half of a forward line, shifted by
+                                                          // 64 bytes against the even half
+    static constexpr int ZS = N + HOFF;                   // forward line stride
     static constexpr int MROWS = R;                        // rows of the M tile per component
     static constexpr int TW_OFF = 0, TA_OFF = L;
     static constexpr int MT_OFF = L + N;                          // float2 units; floats: 3*MROWS*N
     static constexpr int MT_C = 3 * MROWS * N / 2;
     static constexpr int SB_OFF = MT_OFF + MT_C;                  // staged spectrum / new M rows
-    static constexpr int SB_C = cmax<3 * H * R, 3 * R * N / 2>::v;
+    static constexpr int SB_C = cmax<3 * HP * R, 3 * R * N / 2>::v;
     static constexpr int W_OFF = SB_OFF + ((SB_C + 1) / 2) * 2;
     static constexpr int W_C = cmax<cmax<2 * NL * F::EX, NL * L>::v, NL * ZS>::v;
     static constexpr size_t BYTES = sizeof(float2) * (W_OFF + W_C);
@@ -253,6 +257,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
+    constexpr int HM = Lay::HM, HP = Lay::HP, HOFF = Lay::HOFF;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm + Lay::TW_OFF;
     float2* ta = sm + Lay::TA_OFF;
@@ -285,34 +290,40 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     }
     __pipeline_commit();
     pdl_wait();
-    // staged half-spectrum of the H tile: sb[(c*H + kx)*R + r], R-row runs
-    // of the plane kernel's output
-    for (int idx = threadIdx.x; idx < 3 * H * (R / 2); idx += blockDim.x) {
-        const int q = idx % (R / 2), ck = idx / (R / 2);
-        const int c = ck % 3, kx = ck / 3;
-        copy16(sb + (size_t)(c * H + kx) * R + 2 * q, Sh + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * q);
+    // staged half-spectrum of the row pair, split by the parity of kx:
+    // s4[c * HP + pos(kx)] = rows (j0, j0 + 1) of (c, kx), pos(kx) =
+    // (kx & 1) HM + kx / 2, so that the inverse transform below reads
+    // consecutive 16-byte words
+    for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
+        const int c = idx / H, kx = idx - c * H;
+        copy16(sb + (size_t)(c * HP + (kx & 1) * HM + (kx >> 1)) * R,
+               Sh + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0);
     }
     __pipeline_commit();
     __pipeline_wait_prior(0);
     __syncthreads();
 
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
-    const int line = grp >> 1, h = grp & 1;
-    const int lc = line / (R / 2), pr = line % (R / 2);
+    const int line = grp >> 1, h = grp & 1;                 // line = component c of the pair
     const bool fft_thread = grp < 2 * NL;
     float2 v[P];
     float2 w[Q];
-    // ---- inverse x: rebuild Z = A + iB on the full length from the half-spectrum
+    // ---- inverse x: rebuild Z = A + iB (A, B the rows' half-spectra) at
+    // kk = 2 m + h, m = t + Q q: kk <= N reads kx = kk, above it the mirror
+    // kx = L - kk conjugated.  Only q = P/2 straddles kk = N.
     if (fft_thread && t < Q) {
-        const float2* base = sb + (size_t)lc * H * R + 2 * pr;
+        const float4* s4 = reinterpret_cast<const float4*>(sb) + (size_t)line * HP;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            const int kk = 2 * (t + Q * q) + h;
-            const bool low = kk <= N;
-            const int ks = low ? kk : L - kk;
-            float2 A = base[ks * R], B = base[ks * R + 1];
-            if (ks == 0 || ks == N) { A.y = 0.f; B.y = 0.f; }
-            v[q] = low ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+            const int m = t + Q * q;
+            const bool low = q < P / 2 ? true : (q > P / 2 ? false : (h == 0 && t == 0));
+            const int pos = low ? h * HM + m : (h ? HM + N - 1 - m : N - m);
+            float4 ab = s4[pos];
+            if ((q == 0 || q == P / 2) && h == 0 && t == 0) {   // kx = 0 and N: real
+                ab.y = 0.f;
+                ab.w = 0.f;
+            }
+            v[q] = low ? make_float2(ab.x - ab.w, ab.y + ab.z) : make_float2(ab.x + ab.w, ab.z - ab.y);
         }
         F::stepA_tab(v, t, ta, wk + grp * F::EX, true);
     }
@@ -355,8 +366,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         float hd[3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const int ln = cc * (R / 2) + (r >> 1);
-            const float2 z = wk[ln * L + i];
+            const float2 z = wk[cc * L + i];
             hd[cc] = (r & 1) ? z.y : z.x;
         }
         const float bnd = bz + cf.pexch * ((float)((i == 0) + (i == N - 1)) * cf.idx2 +
@@ -394,7 +404,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     __syncthreads();
     // ---- forward x of the new rows (first pass of the next step)
     if (fft_thread && t < Q) {
-        const float* ra = Mn + (size_t)(lc * R + 2 * pr) * N;
+        const float* ra = Mn + (size_t)line * R * N;
         const float* rb = ra + N;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
@@ -409,21 +419,19 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     __syncthreads();
     if (fft_thread && t < P) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) wk[line * ZS + h * N + t + P * q] = w[q];
+        for (int q = 0; q < Q; ++q) wk[line * ZS + h * HOFF + t + P * q] = w[q];   // Z[2 n + h]
     }
     __syncthreads();
     // split each pair into the two rows' half-spectra and store to Snext
-    for (int idx = threadIdx.x; idx < 3 * H * (R / 2); idx += blockDim.x) {
-        const int q = idx % (R / 2);
-        const int rest = idx / (R / 2);
-        const int c = rest % 3, kx = rest / 3;
-        const float2* ln = wk + (c * (R / 2) + q) * ZS;
+    for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
+        const int c = idx / H, kx = idx - c * H;
+        const float2* ln = wk + c * ZS;
         const int km = (L - kx) & (L - 1);
-        const float2 zk = ln[(kx & 1) * N + (kx >> 1)];
-        const float2 zm = ln[(km & 1) * N + (km >> 1)];
+        const float2 zk = ln[(kx & 1) * HOFF + (kx >> 1)];
+        const float2 zm = ln[(km & 1) * HOFF + (km >> 1)];
         const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
                                      0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        *reinterpret_cast<float4*>(Snext + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * q) = o;
+        *reinterpret_cast<float4*>(Snext + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0) = o;
     }
     __syncthreads();
     pdl_trigger();
