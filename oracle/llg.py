@@ -103,6 +103,82 @@ def run_rk(M, nsteps, dt, method, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
     return M
 
 
+# Dormand-Prince embedded Runge-Kutta pair RK5(4) (Dormand and Prince,
+# J. Comput. Appl. Math. 6 (1980) 19-26): nodes c, stage matrix a, fifth-
+# order weights b, and e = b - b_hat, the difference to the embedded
+# fourth-order weights (b_hat_7 = 1/40 acts on the stage at the new state).
+DP_C = (0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0)
+DP_A = (
+    (),
+    (1.0 / 5.0,),
+    (3.0 / 40.0, 9.0 / 40.0),
+    (44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0),
+    (19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0),
+    (9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0),
+)
+DP_B = (35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0)
+DP_E = (71.0 / 57600.0, 0.0, -71.0 / 16695.0, 71.0 / 1920.0, -17253.0 / 339200.0, 22.0 / 525.0, -1.0 / 40.0)
+
+
+def dopri5_step(M, k1, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
+    """One Dormand-Prince step of Eq. (6) (beyond the paper, which uses Euler).
+    Stages at plain (not renormalised) states Y_i = M + dt sum_j a_ij k_j; the
+    fifth-order state M + dt sum_i b_i k_i is renormalised to |M| = Ms; the
+    seventh stage k7 is evaluated there and serves as k1 of the next step
+    (first same as last).  The error estimate is
+      err = max over cells |dt sum_i e_i k_i| / Ms.
+    k1 = f(M) is passed in.  Returns (M_new, err, k7)."""
+    f = lambda X: _rhs(X, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)
+    ks = [k1]
+    for i in range(1, 6):
+        Y = M + dt * sum(DP_A[i][j] * ks[j] for j in range(i))
+        ks.append(f(Y))
+    Y5 = M + dt * sum(DP_B[j] * ks[j] for j in range(6))
+    Mn = Y5 * (Ms / np.sqrt(np.sum(Y5 * Y5, axis=0)))
+    k7 = f(Mn)
+    ks.append(k7)
+    D = dt * sum(DP_E[j] * ks[j] for j in range(7))
+    err = float(np.max(np.sqrt(np.sum(D * D, axis=0)))) / Ms
+    return Mn, err, k7
+
+
+# Step-size controller of the adaptive run: a step is accepted when
+# err <= tol; the next step is h * clamp(0.9 (tol / err)^(1/5), 0.2, 5), with
+# no growth right after a rejection; the last step is shortened to end on
+# t_span.
+DP_SAFETY, DP_FMIN, DP_FMAX = 0.9, 0.2, 5.0
+
+
+def dp_next_factor(err, tol, after_reject):
+    fac = DP_FMAX if err <= 0.0 else DP_SAFETY * (tol / err) ** 0.2
+    fac = min(DP_FMAX, max(DP_FMIN, fac))
+    return min(fac, 1.0) if after_reject else fac
+
+
+def run_dopri5(M, t_span, dt0, tol, max_steps, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
+    """Adaptive Dormand-Prince integration of Eq. (6) over t_span.  Returns
+    (M, dt_next, (accepted, rejected, field evaluations, time covered))."""
+    f = lambda X: _rhs(X, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)
+    k1 = f(M)
+    t, dt, acc, rej, nev = 0.0, dt0, 0, 0, 1
+    after_reject = False
+    while t_span - t > 1e-12 * t_span and acc + rej < max_steps:
+        h = min(dt, t_span - t)
+        Mn, err, k7 = dopri5_step(M, k1, h, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)
+        nev += 6
+        if err <= tol:
+            t += h
+            M, k1 = Mn, k7
+            acc += 1
+            dt = h * dp_next_factor(err, tol, after_reject)
+            after_reject = False
+        else:
+            rej += 1
+            dt = h * dp_next_factor(err, tol, True)
+            after_reject = True
+    return M, dt, (acc, rej, nev, t)
+
+
 def run_euler(M, nsteps, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L):
     for _ in range(nsteps):
         M, _ = euler_step(M, dt, cell, Ms, A, Ku, alpha, gamma, H_ext, Kt, L)

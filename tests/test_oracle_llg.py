@@ -171,3 +171,93 @@ def test_rk_euler_branch_equals_euler_step():
     a = L.rk_step(M, 1e-13, "euler", cell, Ms, A, Ku, alpha, gamma, Hext, Kt, Lp)
     b, _ = L.euler_step(M, 1e-13, cell, Ms, A, Ku, alpha, gamma, Hext, Kt, Lp)
     assert np.max(np.abs(a - b)) < 1e-9 * Ms
+
+
+# ---- adaptive Dormand-Prince integrator (beyond the paper's Euler scheme)
+
+def test_dormand_prince_tableau_order_conditions():
+    """Row sums equal the nodes; the fifth-order weights satisfy the order
+    conditions up to order 5 (the ones for bushy and tall trees checked here),
+    the embedded weights b - e those up to order 4 but not the order-5
+    quadrature condition."""
+    from fractions import Fraction
+    c, A, b, e = L.DP_C, L.DP_A, L.DP_B, L.DP_E
+    for i in range(1, 6):
+        assert abs(sum(A[i]) - c[i]) < 1e-15
+    a = lambda i, j: A[i][j] if i < 6 and j < len(A[i]) else (b[j] if i == 6 else 0.0)
+    bh = [bi - ei for bi, ei in zip(b, e)]
+    for w, top in ((b, 5), (bh, 4)):
+        for q in range(1, top + 1):
+            assert abs(sum(wi * ci ** (q - 1) for wi, ci in zip(w, c)) - 1.0 / q) < 1e-14, (top, q)
+        # sum_i w_i sum_j a_ij c_j = 1/6, sum_i w_i c_i sum_j a_ij c_j = 1/8
+        s6 = sum(w[i] * sum(a(i, j) * c[j] for j in range(i)) for i in range(7))
+        s8 = sum(w[i] * c[i] * sum(a(i, j) * c[j] for j in range(i)) for i in range(7))
+        s12 = sum(w[i] * sum(a(i, j) * c[j] ** 2 for j in range(i)) for i in range(7))
+        assert abs(s6 - 1.0 / 6.0) < 1e-14 and abs(s8 - 1.0 / 8.0) < 1e-14 and abs(s12 - 1.0 / 12.0) < 1e-14
+    # the embedded pair is genuinely of order 4: its order-5 quadrature fails
+    assert abs(sum(wi * ci ** 4 for wi, ci in zip(bh, c)) - 0.2) > 1e-4
+    assert Fraction(e[6]).limit_denominator(100) == Fraction(-1, 40)
+
+
+def _macrospin_setup(theta0, phi0, Ms):
+    cell = (3e-9, 3e-9, 3e-9)
+    Lp = D.default_lengths((1, 1, 1))
+    Kt = D.kernel_spectrum(T.tensor_octant((1, 1, 1), cell), Lp)
+    M = Ms * np.array([np.sin(theta0) * np.cos(phi0), np.sin(theta0) * np.sin(phi0),
+                       np.cos(theta0)]).reshape(3, 1, 1, 1)
+    return cell, Kt, Lp, M
+
+
+def test_dormand_prince_fixed_step_order_and_error_estimate():
+    """Fixed steps on the macrospin: the global error against the closed form
+    falls as dt^5, and the step's error estimate (the fourth-order local
+    error) as dt^5."""
+    theta0, phi0, Hz, alpha, gamma, Ms = 1.2, 0.3, 2e5, 0.1, 2.211e5, 8.6e5
+    cell, Kt, Lp, M0 = _macrospin_setup(theta0, phi0, Ms)
+    args = (cell, Ms, 1.3e-11, 0.0, alpha, gamma, (0.0, 0.0, Hz), Kt, Lp)
+    t_end = 2e-10
+    th, ph = L.macrospin_closed_form(theta0, phi0, Hz, alpha, gamma, t_end)
+    exact = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    errs, ests = [], []
+    for dt in (4e-12, 2e-12, 1e-12):
+        M = M0.copy()
+        k1 = L._rhs(M, *args)
+        first_est = None
+        for _ in range(int(round(t_end / dt))):
+            M, est, k1 = L.dopri5_step(M, k1, dt, *args)
+            if first_est is None:
+                first_est = est
+        errs.append(np.linalg.norm(M.reshape(3) / Ms - exact))
+        ests.append(first_est)
+    for r in (errs[0] / errs[1], errs[1] / errs[2]):
+        assert 0.75 * 32 < r < 1.3 * 32, errs
+    for r in (ests[0] / ests[1], ests[1] / ests[2]):
+        assert 0.75 * 32 < r < 1.3 * 32, ests
+
+
+def test_dormand_prince_adaptive_run_meets_tolerance():
+    """Adaptive runs on the macrospin end within a small multiple of tol of
+    the closed form, and a tighter tol takes more steps, about
+    tol^(-1/5) more."""
+    theta0, phi0, Hz, alpha, gamma, Ms = 1.2, 0.3, 2e5, 0.1, 2.211e5, 8.6e5
+    cell, Kt, Lp, M0 = _macrospin_setup(theta0, phi0, Ms)
+    t_end = 4e-10
+    th, ph = L.macrospin_closed_form(theta0, phi0, Hz, alpha, gamma, t_end)
+    exact = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    steps = []
+    for tol in (1e-6, 1e-8):
+        M, dt_next, (acc, rej, nev, t) = L.run_dopri5(M0.copy(), t_end, 1e-13, tol, 10000, cell, Ms, 1.3e-11, 0.0,
+                                                      alpha, gamma, (0.0, 0.0, Hz), Kt, Lp)
+        assert abs(t - t_end) < 1e-12 * t_end
+        assert nev == 1 + 6 * (acc + rej)
+        err = np.linalg.norm(M.reshape(3) / Ms - exact)
+        assert err < 50 * tol * acc, (tol, err, acc)
+        steps.append(acc)
+    assert 100 ** 0.2 * 0.6 < steps[1] / steps[0] < 100 ** 0.2 * 1.6, steps
+
+
+def test_dormand_prince_controller_factors():
+    assert L.dp_next_factor(0.0, 1e-6, False) == L.DP_FMAX
+    assert L.dp_next_factor(1e-1, 1e-6, False) == L.DP_FMIN
+    assert L.dp_next_factor(1e-9, 1e-6, True) == 1.0
+    assert abs(L.dp_next_factor(1e-6, 1e-6, False) - 0.9) < 1e-15
