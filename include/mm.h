@@ -49,7 +49,8 @@ enum {
     MM_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed      */
     MM_ENONFINITE = -4,   /* a step produced a non-finite magnetisation       */
     MM_ETIMEOUT = -5,     /* a bounded device-side wait gave up               */
-    MM_EUNSUPPORTED = -6  /* a size outside the supported plan limits         */
+    MM_EUNSUPPORTED = -6, /* a size outside the supported plan limits         */
+    MM_ELIMIT = -7        /* an adaptive run used up its step budget          */
 };
 
 typedef struct mm_ctx mm_ctx;
@@ -101,6 +102,36 @@ int mm_destroy(mm_ctx *ctx);
  * Returns MM_EINVAL for an unknown method, MM_ENOMEM on allocation failure.
  */
 int mm_set_integrator(mm_ctx *ctx, int method);
+
+/*
+ * mm_run_adaptive -- integrate Eq. (6) over t_span seconds from the current
+ * M with the embedded Dormand-Prince RK5(4) pair and step-size control
+ * (beyond the paper, whose scheme is forward Euler, Table 1 caption).
+ * Every stage evaluates H_eff of its (plain, not renormalised) stage state
+ * with the three demag/field passes; the fifth-order state is renormalised
+ * to |M| = Ms; the seventh stage is the right-hand side at that state and
+ * is reused as the first stage of the next step.  The error of a trial step
+ * is err = max over cells |dt sum_i e_i k_i| / Ms (e: fifth- minus fourth-
+ * order weights).  A step is accepted when err <= tol; the next trial step
+ * is h * clamp(0.9 (tol / err)^(1/5), 0.2, 5), without growth right after a
+ * rejection; the last step is shortened to end on t_span.
+ *
+ *   t_span     seconds to cover, finite, >= 0 (0: nothing happens).
+ *   dt         in: the first trial step (s, > 0); out: the step the
+ *              controller proposes next (host memory).
+ *   tol        error bound per step, > 0 (dimensionless, relative to Ms).
+ *   max_steps  limit on accepted + rejected trial steps, >= 1.
+ *   stats      NULL or 4 doubles (host): accepted steps, rejected steps,
+ *              field evaluations, seconds covered.
+ *
+ * Synchronises once per trial step (the error estimate is read back to the
+ * host, which runs the controller).  Allocates 8 extra 3*N float32 buffers on
+ * first use.  Returns MM_OK once t_span is covered, MM_ELIMIT when
+ * max_steps ran out first (M is the last accepted state), MM_EINVAL, MM_ENOMEM
+ * or MM_ECUDA.  A non-finite trial state gives an infinite error and is
+ * rejected like any other.
+ */
+int mm_run_adaptive(mm_ctx *ctx, double t_span, double *dt, double tol, int max_steps, double stats[4]);
 
 /* mm_set_field -- uniform external (Zeeman) field H_ext in A/m (Eq. (1),
  * (2)); applies to later steps.  H_ext: 3 doubles, host memory. */

@@ -130,6 +130,20 @@ size_t split_smem_z(const Geom& g);
 cudaError_t launch_rk_stage(int N, const LlgCoef& cf, float a_next, float b_acc, int kind, const float* Mst,
                             const float* H, const float* Mb, float* acc, float* out, int* flag, cudaStream_t s);
 
+// Adaptive Dormand-Prince stages (integrators.cu).
+struct DpPtrs {
+    float* k[7];
+};
+struct DpWeights {
+    float w[7];
+};
+cudaError_t launch_dp_combine(int N, const DpPtrs& kp, const DpWeights& w, int nk, float dt, const float* M,
+                              float* out, cudaStream_t s);
+cudaError_t launch_dp_stage(int N, const LlgCoef& cf, const DpPtrs& kp, int stage, const DpWeights& w, int renorm,
+                            const float* Y, const float* H, const float* M, float* out, int* flag, cudaStream_t s);
+cudaError_t launch_dp_error(int N, const LlgCoef& cf, const DpPtrs& kp, const DpWeights& e, const float* Y,
+                            const float* H, float* k7out, unsigned* errbits, cudaStream_t s);
+
 }  // namespace mmk
 struct mm_fno;
 namespace mmk {

@@ -21,6 +21,7 @@ MM_ECUDA = -3
 MM_ENONFINITE = -4
 MM_ETIMEOUT = -5
 MM_EUNSUPPORTED = -6
+MM_ELIMIT = -7
 
 MM_INTEGRATOR_EULER = 0
 MM_INTEGRATOR_HEUN = 1
@@ -39,6 +40,8 @@ _PROTOS = {
     "mm_demag_field": (_c_int, [_vp, _vp, _vp]),
     "mm_effective_field": (_c_int, [_vp, _vp, _vp]),
     "mm_step": (_c_int, [_vp, _c_int, _c_double]),
+    "mm_run_adaptive": (_c_int, [_vp, _c_double, ctypes.POINTER(_c_double), _c_double, _c_int,
+                                 ctypes.POINTER(_c_double)]),
     "mm_energy": (_c_int, [_vp, ctypes.POINTER(_c_double)]),
     "mm_sync": (_c_int, [_vp]),
     "mm_last_error": (ctypes.c_char_p, [_vp]),
@@ -192,6 +195,19 @@ def mm_effective_field(ctx, M, H):
 
 def mm_step(ctx, n, dt):
     _check(lib().mm_step(ctx.handle, int(n), float(dt)))
+
+
+def mm_run_adaptive(ctx, t_span, dt, tol, max_steps=100000):
+    """Adaptive Dormand-Prince run over t_span seconds.  Returns (complete,
+    dt_next, stats) with stats = dict(accepted, rejected, evaluations, t);
+    complete is False when max_steps ran out first (MM_ELIMIT)."""
+    d = ctypes.c_double(float(dt))
+    st = (ctypes.c_double * 4)()
+    rc = lib().mm_run_adaptive(ctx.handle, float(t_span), ctypes.byref(d), float(tol), int(max_steps), st)
+    if rc != MM_ELIMIT:
+        _check(rc)
+    stats = dict(accepted=int(st[0]), rejected=int(st[1]), evaluations=int(st[2]), t=float(st[3]))
+    return rc == MM_OK, d.value, stats
 
 
 def mm_energy(ctx):
