@@ -62,7 +62,8 @@ def algorithmic_bytes(grid):
       Ks = (Lx/2+1)(Ly/2+1)(Lz/2+1) octant bins x 6 floats.
     Two-kernel power-of-two step (this benchmark):
       K_A plane 48X + 24Kd, K_B x-step 48X + 24N,
-      Kd = (Lx/2+1)(Ly/2+1) nz coupling sets x 6 floats."""
+      Kd = (Lx/2+1)(Ly/2+1) nz coupling sets x 6 floats.
+    Compulsory floor: M in and out (24N) plus the tensor spectrum once."""
     nx, ny, nz = grid
     L = [1 if n == 1 else 2 * n for n in grid]     # power-of-two grids here
     N = nx * ny * nz
@@ -72,7 +73,31 @@ def algorithmic_bytes(grid):
     return {"pass1": 12 * N + 24 * X, "plane3": 48 * X + 24 * Ks, "pass3": 24 * X + 24 * N,
             "step3": 36 * N + 96 * X + 24 * Ks,
             "kA": 48 * X + 24 * Kd, "kB": 48 * X + 24 * N, "step2": 24 * N + 96 * X + 24 * Kd,
-            "demag": 24 * N + 96 * X + 24 * Ks}
+            "demag": 24 * N + 96 * X + 24 * Ks,
+            "floor2": 24 * N + 24 * Kd, "floor3": 24 * N + 24 * Ks}
+
+
+def algorithmic_flops(grid):
+    """Nominal FP32 flops of one two-kernel step, counting a complex FFT of
+    length n as 5 n log2 n and a pruned (zero-padded) transform of length 2n
+    as two of length n:
+      x forward and inverse: 3 ny nz / 2 row pairs, one pruned length-2nx
+        transform each; y forward and inverse: 3 nz (nx + 1) lines of
+        pruned length 2ny; direct z sum: 9 nz^2 complex-by-real
+        multiply-adds (4 flops) per (kx, ky) bin of (nx + 1) x 2ny;
+      field + LLG + Euler + renormalisation: 100 flops per cell."""
+    import math
+    nx, ny, nz = grid
+    fft = lambda n: 5.0 * n * math.log2(n) if n > 1 else 0.0
+    x = 2 * (3 * ny * nz / 2) * 2 * fft(nx)
+    y = 2 * (3 * nz * (nx + 1)) * 2 * fft(ny)
+    z = (nx + 1) * 2 * ny * 9 * nz * nz * 4
+    return x + y + z + 100.0 * nx * ny * nz
+
+
+def alu_peak_tflops(sm_mhz):
+    """FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def measured_peaks():
@@ -311,6 +336,12 @@ def run_gpu(args, rank, ws):
         except Exception:
             traffic = None
     step_ms_mean = 1e3 * t_max / K
+    flops = algorithmic_flops(GRID)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu = {"flops_per_step": flops, "model": "two-kernel, 5 n log2 n per length-n FFT",
+           "achieved_tflops": flops / (step_ms_mean * 1e-3) / 1e12,
+           "peak_tflops": alu_peak_tflops(sm_mhz), "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %g MHz" % sm_mhz}
+    alu["frac"] = alu["achieved_tflops"] / alu["peak_tflops"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": step_ms_mean, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -321,6 +352,10 @@ def run_gpu(args, rank, ws):
                      "frac": step_bytes / (step_ms_mean * 1e-3) / 1e9 / peak,
                      "three_pass_model_bytes": by["step3"],
                      "three_pass_model_frac": by["step3"] / (step_ms_mean * 1e-3) / 1e9 / peak},
+        "compulsory_bytes": {"bytes": by["floor2"] if launches == 2 else by["floor3"],
+                             "what": "M in + M out + tensor spectrum in",
+                             "frac_at_step_time": None},
+        "alu": alu,
         "pass_ms": passes,
         "launches_per_step": launches,
         "steady_state_l2_resident": {"ms_per_step": warm_ms, "cells_steps_per_s": ws * N / (warm_ms * 1e-3)},
@@ -332,6 +367,8 @@ def run_gpu(args, rank, ws):
         "e2e": {"value": ws * N * ke / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N},
     }
+    cb = line["compulsory_bytes"]
+    cb["frac_at_step_time"] = cb["bytes"] / (step_ms_mean * 1e-3) / 1e9 / peak
     if rank == 0 and ws == 1 and not (args.no_cpu_baseline or args.quick):
         rate, n, el = oracle_rate(seconds_budget=args.cpu_seconds)
         line["cpu_baseline"] = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
