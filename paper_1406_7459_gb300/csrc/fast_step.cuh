@@ -1,15 +1,17 @@
 // fast_step.cuh -- the two-kernel Euler step for power-of-two grids.
 //
-// Step n (spectrum S[p] of M^n already formed):
+// Step n (spectrum S of M^n already formed):
 //   K_A  k_plane_pdl   per kx plane: y FFT, the z part of the convolution
 //                      as a direct sum over the nz layers with the (x, y)
 //                      tensor spectrum of each z offset (exact, and cheaper
 //                      than a length-2nz transform pair for nz <= 8), the
-//                      tensor product (Eq. (15)), inverse y; in place on S[p].
+//                      tensor product (Eq. (15)), inverse y; S -> Sh.  The
+//                      zero-padded exchange stencil of Eq. (4) rides in the
+//                      same spectrum.
 //   K_B  k_xstep_pdl   per (layer, row pair): inverse x C2R (Eq. (16)), the
 //                      field and LLG update of Eqs. (2)-(6) with the Euler
 //                      step and renormalisation, and then the forward x R2C
-//                      (Eq. (14)) of the new rows into S[1-p], which is the
+//                      (Eq. (14)) of the new rows into S, which is the
 //                      first pass of step n+1.
 // So a step is two kernels and M^{n+1} is never re-read for its transform.
 //
@@ -17,9 +19,10 @@
 // `griddepcontrol.wait` each one only touches data that no kernel of the
 // previous step writes: K_A prefetches its tensor-spectrum slice and the
 // twiddles; K_B prefetches twiddles and its M^n tile (M^n was written two
-// launches earlier, and K_A does not trigger its dependents before it has
-// passed its own wait, which orders it after that writer).  Each kernel
-// triggers its dependents only after its last global store.
+// launches earlier, and K_A triggers its dependents only once it has passed
+// its own wait, which orders it after that writer).  K_A triggers right
+// after that wait, so K_B's CTAs launch and prefetch while K_A runs; K_B
+// triggers after its last global store.
 #pragma once
 #include <cuda_pipeline.h>
 
