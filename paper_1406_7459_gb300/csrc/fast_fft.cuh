@@ -182,8 +182,11 @@ template <int N> struct Fft2 {
     }
     // Fill ta from the W_{2N} table in global memory (asynchronous 8-byte
     // copies; the caller commits and waits with its other prologue copies).
+    // T: the block size.
+    template <int T>
     static __device__ __forceinline__ void load_ta(float2* ta, const float2* tw_global) {
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+#pragma unroll
+        for (int i = threadIdx.x; i < N; i += T) {
             const int a = i / Q, t = i - a * Q;
             __pipeline_memcpy_async(ta + i, tw_global + 2 * t * a, sizeof(float2));
         }

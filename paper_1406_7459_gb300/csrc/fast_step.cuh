@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     using Lay = PlaneLayout<NY, NZ>;
     using F = Fft2<NY>;
     constexpr int P = F::P, Q = F::Q, G = F::G, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
+    constexpr int T = Lay::THREADS;                       // the launch's block size
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm + Lay::TW_OFF;
     float2* ta = sm + Lay::TA_OFF;
@@ -118,11 +119,13 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
 
     // prologue: constant data only (twiddles, this kx's slice of the 2-D
     // spectrum), asynchronous, so that it overlaps the wait and the S load
-    for (int i = threadIdx.x; i < LY / 2; i += blockDim.x) copy16(tw + 2 * i, g.twy + 2 * i);
-    F::load_ta(ta, g.twy);
+#pragma unroll
+    for (int i = threadIdx.x; i < LY / 2; i += T) copy16(tw + 2 * i, g.twy + 2 * i);
+    F::template load_ta<T>(ta, g.twy);
     {
         const float* Kp = g.Kd + (size_t)kx * Lay::KT_FLOATS;
-        for (int i = threadIdx.x; i < Lay::KT_FLOATS / 4; i += blockDim.x) copy16(Ks + 4 * i, Kp + 4 * i);
+#pragma unroll
+        for (int i = threadIdx.x; i < Lay::KT_FLOATS / 4; i += T) copy16(Ks + 4 * i, Kp + 4 * i);
     }
     __pipeline_commit();
     pdl_wait();
@@ -157,7 +160,8 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     __syncthreads();
     // z part of the convolution: direct sum over the layers, one (ky)
     // column per task, read and written back by the same thread
-    for (int col = threadIdx.x; col < LY; col += blockDim.x) {
+#pragma unroll
+    for (int col = threadIdx.x; col < LY; col += T) {
         const int hh = col / NY, mm = col - hh * NY;      // ky = 2 mm + hh
         const int ky = 2 * mm + hh;
         const int e = hh * NY + mm;
@@ -223,7 +227,8 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
             for (int q = 0; q < Q; ++q) zb[line * ZS + h * NY + t + P * q] = w[q];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
+#pragma unroll
+        for (int idx = threadIdx.x; idx < NL * NY; idx += T) {
             const int l = idx / NY, n = idx % NY;
             outp[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + NY + n]);
         }
@@ -260,6 +265,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
+    constexpr int T = Lay::THREADS;                       // the launch's block size
     constexpr int HM = Lay::HM, HP = Lay::HP, HOFF = Lay::HOFF;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm + Lay::TW_OFF;
@@ -279,11 +285,13 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     // stencil of Eq. (4) is folded into the 2-D spectrum as the zero-padded
     // stencil, so no neighbour rows are needed; what remains of the
     // free-boundary rule is local (see the field loop below).
-    for (int i = threadIdx.x; i < L / 2; i += blockDim.x) copy16(tw + 2 * i, g.twx + 2 * i);
-    F::load_ta(ta, g.twx);
+#pragma unroll
+    for (int i = threadIdx.x; i < L / 2; i += T) copy16(tw + 2 * i, g.twx + 2 * i);
+    F::template load_ta<T>(ta, g.twx);
     {
         constexpr int CH = N / 4;                               // 16-byte chunks per row
-        for (int idx = threadIdx.x; idx < 3 * R * CH; idx += blockDim.x) {
+#pragma unroll
+        for (int idx = threadIdx.x; idx < 3 * R * CH; idx += T) {
             const int ch = idx % CH;
             const int row = (idx / CH) % R;
             const int c = idx / (CH * R);
@@ -297,7 +305,8 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     // s4[c * HP + pos(kx)] = rows (j0, j0 + 1) of (c, kx), pos(kx) =
     // (kx & 1) HM + kx / 2, so that the inverse transform below reads
     // consecutive 16-byte words
-    for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < 3 * H; idx += T) {
         const int c = idx / H, kx = idx - c * H;
         copy16(sb + (size_t)(c * HP + (kx & 1) * HM + (kx >> 1)) * R,
                Sh + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0);
@@ -351,7 +360,8 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
             for (int q = 0; q < Q; ++q) wk[line * L + h * N + t + P * q] = w[q];   // ob[line][h][n]
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < NL * N; idx += blockDim.x) {
+#pragma unroll
+        for (int idx = threadIdx.x; idx < NL * N; idx += T) {
             const int ln = idx / N, n = idx % N;
             wk[ln * L + n] = cadd(wk[ln * L + n], wk[ln * L + N + n]);
         }
@@ -362,7 +372,8 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     // free face lacks that neighbour, whose term in Eq. (4) is M(i) itself
     // (zero change), so each missing neighbour adds pexch M(i) / delta^2.
     const float bz = cf.pexch * (float)((g.nz > 1) * ((k == 0) + (k == g.nz - 1))) * cf.idz2;
-    for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < R * N; idx += T) {
         const int r = idx / N;
         const int i = idx % N;
         const int j = j0 + r;
@@ -426,7 +437,8 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     }
     __syncthreads();
     // split each pair into the two rows' half-spectra and store to Snext
-    for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < 3 * H; idx += T) {
         const int c = idx / H, kx = idx - c * H;
         const float2* ln = wk + c * ZS;
         const int km = (L - kx) & (L - 1);
