@@ -135,10 +135,20 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
 
     const float2* plane = S + (size_t)kx * NL * g.Jst;
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
-    const int line = grp >> 1, h = grp & 1;
+    const int line = grp >> 1, h = grp & 1;               // inverse y: a line's halves in one warp
+    // forward y: where the groups of a warp can share the half, they do, so
+    // that the odd half's twiddle multiply does not diverge within a warp
+    constexpr int GW = G <= 32 ? 32 / G : 1;              // groups per warp
+    constexpr bool UNI = GW >= 2 && NL % GW == 0;
+    int lf = line, hf = h;
+    if constexpr (UNI) {
+        const int wq = grp / GW, s = grp % GW;
+        hf = wq & 1;
+        lf = (wq >> 1) * GW + s;
+    }
     float2 v[P];
     if (t < Q) {
-        const float2* src = plane + (size_t)line * g.Jst;
+        const float2* src = plane + (size_t)lf * g.Jst;
 #pragma unroll
         for (int q = 0; q < P; ++q) v[q] = src[t + Q * q];
     }
@@ -146,7 +156,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     __syncthreads();
     // forward y (pruned input): odd half pre-multiplied by W_LY^j
     if (t < Q) {
-        if (h) F::odd_input_tab(v, t, tw);
+        if (hf) F::odd_input_tab(v, t, tw);
         F::stepA_tab(v, t, ta, ex + grp * F::EX, false);
     }
     __syncthreads();
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     __syncthreads();
     if (t < P) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) zb[line * ZS + h * NY + t + P * q] = w[q];
+        for (int q = 0; q < Q; ++q) zb[lf * ZS + hf * NY + t + P * q] = w[q];
     }
     __syncthreads();
     // z part of the convolution: direct sum over the layers, one (ky)
