@@ -20,9 +20,9 @@
 // previous step writes: K_A prefetches its tensor-spectrum slice and the
 // twiddles; K_B prefetches twiddles and its M^n tile (M^n was written two
 // launches earlier, and K_A triggers its dependents only once it has passed
-// its own wait, which orders it after that writer).  K_A triggers right
-// after that wait, so K_B's CTAs launch and prefetch while K_A runs; K_B
-// triggers after its last global store.
+// its own wait, which orders it after that writer).  Each kernel triggers
+// after its last global store (kEarlyTrigger moves K_A's trigger up to
+// its wait), so the next kernel's launch and prologue overlap its tail.
 #pragma once
 #include <cuda_pipeline.h>
 
@@ -40,8 +40,15 @@ template <int a, int b> struct cmax { static constexpr int v = a > b ? a : b; };
 
 // Rows of one x-step tile (row pairs pack two real rows into one complex
 // transform).  Both kernels keep the spectrum as [kx][c][k][j]: a plane
-// reads and writes whole lines, an x-step tile gathers R-row runs.
-constexpr int kStepRows = 2;
+// reads and writes whole lines, an x-step tile gathers and scatters R-row
+// runs (32 bytes for four rows: one sector per (c, kx)).
+constexpr int kStepRows = 4;
+
+// The plane kernel lets the x-step launch right after its own wait (true)
+// or only at its end (false).  With four-row tiles the late trigger wins:
+// x-step tiles launched early pile onto the SMs that hold one plane tile and
+// unbalance the x-step; launched at the end they spread evenly.
+constexpr bool kEarlyTrigger = false;
 
 // ------------------------------------------------------------- K_A plane --
 template <int NY, int NZ> struct PlaneLayout {
@@ -131,7 +138,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     pdl_wait();
     // S of the previous x-step is complete: the next kernel may launch and
     // run its prologue (it reads nothing this kernel writes before its own wait)
-    pdl_trigger();
+    if constexpr (kEarlyTrigger) pdl_trigger();
 
     const float2* plane = S + (size_t)kx * NL * g.Jst;
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
@@ -243,11 +250,12 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
             outp[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + NY + n]);
         }
     }
+    if constexpr (!kEarlyTrigger) pdl_trigger();
 }
 
 // ------------------------------------------------------------- K_B xstep --
 template <int N, int R> struct XstepLayout {
-    static_assert(R == 2, "one row pair per tile: the pair shares one complex transform");
+    static_assert(R == 2 || R == 4, "row pairs per tile: a pair shares one complex transform");
     using F = Fft2<N>;
     static constexpr int L = 2 * N, H = N + 1, NL = 3 * R / 2;
     static constexpr int HM = N / 2 + 1;                  // staged kx per parity: kx = 2 m + parity
@@ -271,12 +279,12 @@ template <int N, int R>
 __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     k_xstep_pdl(Geom g, LlgCoef cf, const float2* __restrict__ Sh, float2* __restrict__ Snext,
                 const float* __restrict__ M, float* __restrict__ Mout, int* __restrict__ flag) {
-    static_assert(R == kStepRows, "tile rows match the plane kernel's output layout");
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
     constexpr int T = Lay::THREADS;                       // the launch's block size
     constexpr int HM = Lay::HM, HP = Lay::HP, HOFF = Lay::HOFF;
+    constexpr int RP = R / 2;                             // row pairs of the tile
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm + Lay::TW_OFF;
     float2* ta = sm + Lay::TA_OFF;
@@ -311,22 +319,25 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     }
     __pipeline_commit();
     pdl_wait();
-    // staged half-spectrum of the row pair, split by the parity of kx:
-    // s4[c * HP + pos(kx)] = rows (j0, j0 + 1) of (c, kx), pos(kx) =
-    // (kx & 1) HM + kx / 2, so that the inverse transform below reads
-    // consecutive 16-byte words
+    // staged half-spectrum of the tile, split by the parity of kx:
+    // s4[(c * HP + pos(kx)) * RP + pr] = rows (j0 + 2 pr, j0 + 2 pr + 1) of
+    // (c, kx), pos(kx) = (kx & 1) HM + kx / 2, so that the inverse transform
+    // below reads consecutive 16-byte words (every RP-th one); the RP chunks
+    // of one (c, kx) are adjacent in global memory and go to adjacent lanes
 #pragma unroll
-    for (int idx = threadIdx.x; idx < 3 * H; idx += T) {
-        const int c = idx / H, kx = idx - c * H;
-        copy16(sb + (size_t)(c * HP + (kx & 1) * HM + (kx >> 1)) * R,
-               Sh + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0);
+    for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
+        const int pr = idx % RP, ck = idx / RP;
+        const int c = ck / H, kx = ck - c * H;
+        copy16(sb + ((size_t)(c * HP + (kx & 1) * HM + (kx >> 1)) * RP + pr) * 2,
+               Sh + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * pr);
     }
     __pipeline_commit();
     __pipeline_wait_prior(0);
     __syncthreads();
 
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
-    const int line = grp >> 1, h = grp & 1;                 // line = component c of the pair
+    const int line = grp >> 1, h = grp & 1;                 // line = c * RP + pr
+    const int lc = line / RP, pr = line % RP;
     const bool fft_thread = grp < 2 * NL;
     float2 v[P];
     float2 w[Q];
@@ -334,13 +345,13 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     // kk = 2 m + h, m = t + Q q: kk <= N reads kx = kk, above it the mirror
     // kx = L - kk conjugated.  Only q = P/2 straddles kk = N.
     if (fft_thread && t < Q) {
-        const float4* s4 = reinterpret_cast<const float4*>(sb) + (size_t)line * HP;
+        const float4* s4 = reinterpret_cast<const float4*>(sb) + (size_t)lc * HP * RP + pr;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int m = t + Q * q;
             const bool low = q < P / 2 ? true : (q > P / 2 ? false : (h == 0 && t == 0));
             const int pos = low ? h * HM + m : (h ? HM + N - 1 - m : N - m);
-            float4 ab = s4[pos];
+            float4 ab = s4[pos * RP];
             if ((q == 0 || q == P / 2) && h == 0 && t == 0) {   // kx = 0 and N: real
                 ab.y = 0.f;
                 ab.w = 0.f;
@@ -390,7 +401,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         float hd[3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const float2 z = wk[cc * L + i];
+            const float2 z = wk[(cc * RP + (r >> 1)) * L + i];   // pair line of rows (r & ~1, r | 1)
             hd[cc] = (r & 1) ? z.y : z.x;
         }
         const float bnd = bz + cf.pexch * ((float)((i == 0) + (i == N - 1)) * cf.idx2 +
@@ -428,7 +439,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     __syncthreads();
     // ---- forward x of the new rows (first pass of the next step)
     if (fft_thread && t < Q) {
-        const float* ra = Mn + (size_t)line * R * N;
+        const float* ra = Mn + (size_t)(lc * R + 2 * pr) * N;
         const float* rb = ra + N;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
@@ -446,17 +457,20 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         for (int q = 0; q < Q; ++q) wk[line * ZS + h * HOFF + t + P * q] = w[q];   // Z[2 n + h]
     }
     __syncthreads();
-    // split each pair into the two rows' half-spectra and store to Snext
+    // split each pair into the two rows' half-spectra and store to Snext;
+    // the RP pairs of one (c, kx) are adjacent in global memory and go to
+    // adjacent lanes
 #pragma unroll
-    for (int idx = threadIdx.x; idx < 3 * H; idx += T) {
-        const int c = idx / H, kx = idx - c * H;
-        const float2* ln = wk + c * ZS;
+    for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
+        const int p2 = idx % RP, ck = idx / RP;
+        const int c = ck / H, kx = ck - c * H;
+        const float2* ln = wk + (c * RP + p2) * ZS;
         const int km = (L - kx) & (L - 1);
         const float2 zk = ln[(kx & 1) * HOFF + (kx >> 1)];
         const float2 zm = ln[(km & 1) * HOFF + (km >> 1)];
         const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
                                      0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        *reinterpret_cast<float4*>(Snext + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0) = o;
+        *reinterpret_cast<float4*>(Snext + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * p2) = o;
     }
     __syncthreads();
     pdl_trigger();
