@@ -296,8 +296,12 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     const int jt = blockIdx.x % ntj;
     const int k = blockIdx.x / ntj;
     const int j0 = jt * R;
-    const size_t Nc = (size_t)g.N;
-    const size_t plane_xy = (size_t)N * g.ny;
+    // 32-bit offsets: the plan admits this kernel only when 3 (nx + 1) nz ny
+    // complex values and 3 nx ny nz floats index below 2^31
+    const int Nc = g.N;
+    const int plane_xy = N * g.ny;
+    const int s_c = g.nz * g.Jst, s_kx = 3 * s_c;            // spectrum strides of c and kx
+    const int s_base = k * g.Jst + j0;
 
     // prologue: twiddles and the tile's own M^n rows.  The exchange
     // stencil of Eq. (4) is folded into the 2-D spectrum as the zero-padded
@@ -313,8 +317,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
             const int ch = idx % CH;
             const int row = (idx / CH) % R;
             const int c = idx / (CH * R);
-            copy16(Mt + ((size_t)c * R + row) * N + 4 * ch,
-                   M + c * Nc + (size_t)k * plane_xy + (size_t)(j0 + row) * N + 4 * ch);
+            copy16(Mt + (c * R + row) * N + 4 * ch, M + c * Nc + k * plane_xy + (j0 + row) * N + 4 * ch);
         }
     }
     __pipeline_commit();
@@ -328,8 +331,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
         const int pr = idx % RP, ck = idx / RP;
         const int c = ck / H, kx = ck - c * H;
-        copy16(sb + ((size_t)(c * HP + (kx & 1) * HM + (kx >> 1)) * RP + pr) * 2,
-               Sh + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * pr);
+        copy16(sb + ((c * HP + (kx & 1) * HM + (kx >> 1)) * RP + pr) * 2, Sh + kx * s_kx + c * s_c + s_base + 2 * pr);
     }
     __pipeline_commit();
     __pipeline_wait_prior(0);
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         float m[3], hh[3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const float m0 = Mt[((size_t)cc * R + r) * N + i];
+            const float m0 = Mt[(cc * R + r) * N + i];
             m[cc] = m0;
             hh[cc] = hd[cc] + bnd * m0;
         }
@@ -427,8 +429,8 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         const float n2 = m[2] + cf.dt * (cf.c1 * p2 + cf.c2 * q2);
         const float s = cf.Ms * rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
         const float o0 = n0 * s, o1 = n1 * s, o2 = n2 * s;
-        if (!(isfinite(o0) && isfinite(o1) && isfinite(o2))) atomicOr(flag, 1);
-        const size_t cell = (size_t)i + (size_t)N * ((size_t)j0 + r) + plane_xy * k;
+        if (!isfinite(o0 + o1 + o2)) atomicOr(flag, 1);     // |o| <= Ms when finite
+        const int cell = i + N * (j0 + r) + plane_xy * k;
         Mout[cell] = o0;
         Mout[Nc + cell] = o1;
         Mout[2 * Nc + cell] = o2;
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         const float2 zm = ln[(km & 1) * HOFF + (km >> 1)];
         const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
                                      0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        *reinterpret_cast<float4*>(Snext + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j0 + 2 * p2) = o;
+        *reinterpret_cast<float4*>(Snext + kx * s_kx + c * s_c + s_base + 2 * p2) = o;
     }
     __syncthreads();
     pdl_trigger();

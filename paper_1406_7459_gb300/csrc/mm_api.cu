@@ -192,6 +192,8 @@ static int build_plan(mm_ctx* c) {
         bool ok = fast_step_lookup_x(g.nx, &s);
         ok = ok && (fast_step_lookup_plane_a(g.ny, g.nz, &s) || fast_step_lookup_plane_b(g.ny, g.nz, &s));
         ok = ok && l.fx && !l.split && g.ny % s.rb == 0 && s.sa <= smem_cap && s.sb <= smem_cap;
+        // the x-step kernel indexes the spectrum and M with 32-bit offsets
+        ok = ok && 3.0 * g.Hx * g.nz * g.Jst < (double)INT_MAX && 3.0 * g.N < (double)INT_MAX;
         c->has_fs = ok;
     }
     return MM_OK;
