@@ -62,10 +62,27 @@ cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
     return cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem2);
 }
 
+// Launch configuration with programmatic serialisation: the compile-time
+// pass kernels wait on griddepcontrol before touching M, S or their output,
+// so each may start while the previous kernel on the stream drains.
+static cudaLaunchConfig_t pdl_cfg(int grid, int threads, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s) {
     if (l.fx) {
-        l.fx->p1<<<3 * g.nz * (g.ny / l.fx->r1), l.fx->t1, l.fx->s1, s>>>(g, M, S);
-        return cudaGetLastError();
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = pdl_cfg(3 * g.nz * (g.ny / l.fx->r1), l.fx->t1, l.fx->s1, s, attr);
+        return cudaLaunchKernelEx(&cfg, l.fx->p1, g, M, S);
     }
     const int ntj = (g.ny + l.r1 - 1) / l.r1;
     k_pass1<<<3 * g.nz * ntj, l.t1, l.smem1, s>>>(g, l.r1, l.g1, M, S);
@@ -75,8 +92,9 @@ cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2*
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s) {
     if (l.split) return launch_split_plane(g, S, s);
     if (l.fp) {
-        l.fp->pl<<<g.Hx, l.fp->t2, l.fp->s2, s>>>(g, S);
-        return cudaGetLastError();
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = pdl_cfg(g.Hx, l.fp->t2, l.fp->s2, s, attr);
+        return cudaLaunchKernelEx(&cfg, l.fp->pl, g, S);
     }
     PlaneFn pf = plane_fn(g.Lz);
     if (!pf) return cudaErrorInvalidValue;
@@ -87,8 +105,9 @@ cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t
 cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int mode, const float2* S,
                          const float* M, float* out, int* flag, cudaStream_t s) {
     if (l.fx) {
-        l.fx->p3[mode]<<<g.nz * (g.ny / l.fx->r3), l.fx->t3, l.fx->s3, s>>>(g, c, S, M, out, flag);
-        return cudaGetLastError();
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = pdl_cfg(g.nz * (g.ny / l.fx->r3), l.fx->t3, l.fx->s3, s, attr);
+        return cudaLaunchKernelEx(&cfg, l.fx->p3[mode], g, c, S, M, out, flag);
     }
     const int ntj = (g.ny + l.r3 - 1) / l.r3;
     const int grid = g.nz * ntj;

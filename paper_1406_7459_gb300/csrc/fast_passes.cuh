@@ -16,6 +16,13 @@
 
 namespace mmk {
 
+// Programmatic dependent launch: a kernel launched with the programmatic-
+// serialisation attribute may start while its predecessor drains; it must
+// call pdl_wait() before it reads or writes anything the predecessor may
+// touch.  pdl_trigger() lets the successor launch early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // shared-memory padding of a spectrum line: one slot every 16
 __device__ __forceinline__ int pz(int k) { return k + (k >> 4); }
 __host__ __device__ constexpr int pzlen(int L) { return L + L / 16 + 1; }
@@ -40,6 +47,7 @@ __global__ void __launch_bounds__(R * Fft2<N>::G) k_pass1_fast(Geom g, const flo
     const int c = b / g.nz;
     const int j0 = jt * R;
     for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = __ldg(g.twx + i);
+    pdl_wait();                           // M and S may belong to the previous kernel
     __syncthreads();
 
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
@@ -165,6 +173,7 @@ __global__ void __launch_bounds__(6 * NZ * Fft2<NY>::G, (6 * NZ * Fft2<NY>::G <=
     const int kx = blockIdx.x;
     float2* plane = S + (size_t)kx * NL * g.Jst;
     for (int i = threadIdx.x; i < LY; i += blockDim.x) tw[i] = __ldg(g.twy + i);
+    pdl_wait();                           // S comes from the previous kernel
     __syncthreads();
 
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
@@ -250,6 +259,7 @@ __global__ void __launch_bounds__(256) k_pass3_fast(Geom g, LlgCoef cf, const fl
     const int k = blockIdx.x / ntj;
     const int j0 = jt * R;
     for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = __ldg(g.twx + i);
+    pdl_wait();                           // S (and M) come from earlier kernels
     for (int idx = threadIdx.x; idx < 3 * H * R; idx += blockDim.x) {
         const int r = idx % R;
         const int rest = idx / R;

@@ -30,8 +30,6 @@
 
 namespace mmk {
 
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // 16-byte asynchronous copies global -> shared (both 16-byte aligned).
 __device__ __forceinline__ void copy16(void* dst, const void* src) { __pipeline_memcpy_async(dst, src, 16); }
