@@ -55,6 +55,7 @@ cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem3);
         if (e != cudaSuccess) return e;
     }
+    if (l.split && l.fs2) return configure_fast_split(*l.fs2);
     if (l.split) return configure_split_kernels(g);
     if (l.fp) return cudaFuncSetAttribute(l.fp->pl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.fp->s2);
     PlaneFn pf = plane_fn(g.Lz);
@@ -90,6 +91,7 @@ cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2*
 }
 
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s) {
+    if (l.split && l.fs2) return launch_fast_split(g, *l.fs2, S, s);
     if (l.split) return launch_split_plane(g, S, s);
     if (l.fp) {
         cudaLaunchAttribute attr[1];

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(R * Fft2<N>::G) k_pass1_fast(Geom g, const flo
                                                                 float2* __restrict__ S) {
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = 2 * N, ZS = pzlen(2 * N);
+    constexpr int T = R * G;                              // the launch's block size
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* ex = tw + L;
@@ -46,7 +47,8 @@ __global__ void __launch_bounds__(R * Fft2<N>::G) k_pass1_fast(Geom g, const flo
     const int k = b % g.nz;
     const int c = b / g.nz;
     const int j0 = jt * R;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = __ldg(g.twx + i);
+#pragma unroll
+    for (int i = threadIdx.x; i < L; i += T) tw[i] = __ldg(g.twx + i);
     pdl_wait();                           // M and S may belong to the previous kernel
     __syncthreads();
 
@@ -73,7 +75,8 @@ __global__ void __launch_bounds__(R * Fft2<N>::G) k_pass1_fast(Geom g, const flo
     }
     __syncthreads();
     // A[k] = (Z[k] + conj Z[L-k]) / 2 (even row), B[k] = -i (Z[k] - conj Z[L-k]) / 2
-    for (int idx = threadIdx.x; idx < (N + 1) * R; idx += blockDim.x) {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < (N + 1) * R; idx += T) {
         const int r = idx % R;
         const int kx = idx / R;
         const float2* line = zb + (r >> 1) * ZS;
@@ -166,13 +169,15 @@ template <int NY, int NZ>
 __global__ void __launch_bounds__(6 * NZ * Fft2<NY>::G, (6 * NZ * Fft2<NY>::G <= 512) ? 2 : 1) k_plane_fast(Geom g, float2* __restrict__ S) {
     using F = Fft2<NY>;
     constexpr int P = F::P, Q = F::Q, G = F::G, LY = 2 * NY, ZS = pzlen(2 * NY), NL = 3 * NZ;
+    constexpr int T = 6 * NZ * G;                         // the launch's block size
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* ex = tw + LY;
     float2* zb = ex + 2 * NL * F::EX;
     const int kx = blockIdx.x;
     float2* plane = S + (size_t)kx * NL * g.Jst;
-    for (int i = threadIdx.x; i < LY; i += blockDim.x) tw[i] = __ldg(g.twy + i);
+#pragma unroll
+    for (int i = threadIdx.x; i < LY; i += T) tw[i] = __ldg(g.twy + i);
     pdl_wait();                           // S comes from the previous kernel
     __syncthreads();
 
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(6 * NZ * Fft2<NY>::G, (6 * NZ * Fft2<NY>::G <=
     __syncthreads();
     // z transform + tensor product + inverse z, one ky column per thread
     const float* Kp = g.Kt + (size_t)kx * g.Hz * g.Hy * 6;
-    for (int ky = threadIdx.x; ky < LY; ky += blockDim.x) {
+    for (int ky = threadIdx.x; ky < LY; ky += T) {
         float2 m[3][NZ];
         const int e = pz(ky);
 #pragma unroll
@@ -234,13 +239,17 @@ __global__ void __launch_bounds__(6 * NZ * Fft2<NY>::G, (6 * NZ * Fft2<NY>::G <=
         }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < NL * NY; idx += T) {
         const int l = idx / NY, n = idx % NY;
         plane[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + pz(n)], zb[l * ZS + pz(NY + n)]);
     }
 }
 
 // ---------------------------------------------------------------- pass 3 --
+template <int N, int R> __host__ __device__ constexpr int pass3_fast_threads() {
+    return 3 * R * Fft2<N>::G > 128 ? 3 * R * Fft2<N>::G : 128;
+}
 // CTA tile: layer k, rows j0..j0+R-1, all three components: 3R/2 complex
 // lines (row pairs), groups (line, half).  Then the per-cell update.
 template <int N, int R, int MODE>
@@ -249,6 +258,7 @@ __global__ void __launch_bounds__(256) k_pass3_fast(Geom g, LlgCoef cf, const fl
                                                      int* __restrict__ flag) {
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = 2 * N, NL = 3 * R / 2, H = N + 1;
+    constexpr int T = pass3_fast_threads<N, R>();         // the launch's block size
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* sb = tw + L;                  // staged half-spectrum [c][kx][r]
@@ -258,9 +268,11 @@ __global__ void __launch_bounds__(256) k_pass3_fast(Geom g, LlgCoef cf, const fl
     const int jt = blockIdx.x % ntj;
     const int k = blockIdx.x / ntj;
     const int j0 = jt * R;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = __ldg(g.twx + i);
+#pragma unroll
+    for (int i = threadIdx.x; i < L; i += T) tw[i] = __ldg(g.twx + i);
     pdl_wait();                           // S (and M) come from earlier kernels
-    for (int idx = threadIdx.x; idx < 3 * H * R; idx += blockDim.x) {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < 3 * H * R; idx += T) {
         const int r = idx % R;
         const int rest = idx / R;
         const int kx = rest % H, c = rest / H;
@@ -300,7 +312,8 @@ __global__ void __launch_bounds__(256) k_pass3_fast(Geom g, LlgCoef cf, const fl
     __syncthreads();
 
     const size_t Nc = (size_t)g.N;
-    for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < R * N; idx += T) {
         const int r = idx / N;
         const int i = idx % N;
         const int j = j0 + r;

@@ -73,15 +73,15 @@ template <int NY, int NZ> struct PlaneLayout {
 // D(dz) from the stored d(|dz|) = (xx, xy, xz, yy, yz, zz): row x uses
 // (xx, xy, xz), row y (xy, yy, yz), row z' (-xz, -yz, zz); xz and yz change
 // sign for dz < 0 (odd in z) and xy, yz for a mirrored ky (odd in y).
-template <int NZ>
-__device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], const float (&d)[NZ][6], int a,
-                                             float2 (&h)[NZ]) {
+// coef(dz, c) gives d_c(dz) with the ky mirror sign already applied.
+template <int NZ, class Coef>
+__device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], Coef coef, int a, float2 (&h)[NZ]) {
 #pragma unroll
     for (int k = 0; k < NZ; ++k) h[k] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int dz = 0; dz < NZ; ++dz) {
-        const float xx = d[dz][0], xy = d[dz][1], xz = d[dz][2];
-        const float yy = d[dz][3], yz = d[dz][4], zz = d[dz][5];
+        const float xx = coef(dz, 0), xy = coef(dz, 1), xz = coef(dz, 2);
+        const float yy = coef(dz, 3), yz = coef(dz, 4), zz = coef(dz, 5);
         float cb0, cb1, cb2;                              // D_a,b for b = x, y, z' at +dz
         float ob0, ob1, ob2;                              // sign-adjusted for -dz
         if (a == 0) { cb0 = xx; cb1 = xy; cb2 = xz; ob0 = xx; ob1 = xy; ob2 = -xz; }
@@ -190,21 +190,25 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         int kyp = ky;
         float sy = 1.f;
         if (2 * ky > LY) { kyp = LY - ky; sy = -1.f; }
-        // the column's couplings, read once for the three output components
-        float d[NZ][6];
+        // the column's couplings: read once for the three output components
+        // when registers allow (nz <= 4), else per component
+        constexpr bool HOIST = NZ <= 4;
+        float d[HOIST ? NZ : 1][6];
+        if constexpr (HOIST) {
 #pragma unroll
-        for (int dz = 0; dz < NZ; ++dz)
+            for (int dz = 0; dz < NZ; ++dz)
 #pragma unroll
-            for (int c = 0; c < 6; ++c) d[dz][c] = Ks[(dz * 6 + c) * Lay::HYP + kyp];
-#pragma unroll
-        for (int dz = 0; dz < NZ; ++dz) {
-            d[dz][1] *= sy;
-            d[dz][4] *= sy;
+                for (int c = 0; c < 6; ++c)
+                    d[dz][c] = (c == 1 || c == 4 ? sy : 1.f) * Ks[(dz * 6 + c) * Lay::HYP + kyp];
         }
+        auto coef = [&](int dz, int c) -> float {
+            if constexpr (HOIST) return d[dz][c];
+            return (c == 1 || c == 4 ? sy : 1.f) * Ks[(dz * 6 + c) * Lay::HYP + kyp];
+        };
         float2 hres[NZ];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            zdirect_task<NZ>(m, d, a, hres);
+            zdirect_task<NZ>(m, coef, a, hres);
 #pragma unroll
             for (int k = 0; k < NZ; ++k) {
                 const float2 o = (a == 2) ? make_float2(hres[k].y, -hres[k].x) : hres[k];   // -i H_z'

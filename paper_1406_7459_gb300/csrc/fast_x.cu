@@ -15,7 +15,7 @@ static void fill_x(FastFns* f) {
     f->p3[kModeHeff] = k_pass3_fast<N, R3, kModeHeff>;
     f->p3[kModeStep] = k_pass3_fast<N, R3, kModeStep>;
     f->r3 = R3;
-    f->t3 = 3 * R3 * Fft2<N>::G > 128 ? 3 * R3 * Fft2<N>::G : 128;
+    f->t3 = pass3_fast_threads<N, R3>();
     f->s3 = pass3_fast_smem<N, R3>();
 }
 

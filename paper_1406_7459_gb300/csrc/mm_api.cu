@@ -63,6 +63,7 @@ struct mm_ctx {
     bool use_graphs = true;
     FastFns fast;              // compile-time kernels (when the grid has them)
     FastStepFns fs;            // two-kernel step (power-of-two grids)
+    FastSplitFns fsplit;       // compile-time split pass 2 (thick power-of-two samples)
     bool has_fs = false;
     float2* Sh = nullptr;      // plane-kernel output of the two-kernel step (layout of S)
     int method = MM_INTEGRATOR_EULER;
@@ -174,6 +175,7 @@ static int build_plan(mm_ctx* c) {
     const bool allow_fast = !(nofast && nofast[0] == '1');
     l.fx = nullptr;
     l.fp = nullptr;
+    l.fs2 = nullptr;
     if (allow_fast) {
         FastFns& f = c->fast;
         if (fast_lookup_x(g.nx, &f) && g.ny % f.r1 == 0 && g.ny % f.r3 == 0 && f.s1 <= smem_cap &&
@@ -188,6 +190,9 @@ static int build_plan(mm_ctx* c) {
             default: break;
         }
         if (pl && f.s2 <= smem_cap && !l.split) l.fp = &f;
+        if (l.split && fast_split_lookup(g.ny, g.nz, &c->fsplit) && c->fsplit.sy <= smem_cap &&
+            c->fsplit.sz <= smem_cap)
+            l.fs2 = &c->fsplit;
         FastStepFns& s = c->fs;
         bool ok = fast_step_lookup_x(g.nx, &s);
         ok = ok && (fast_step_lookup_plane_a(g.ny, g.nz, &s) || fast_step_lookup_plane_b(g.ny, g.nz, &s));

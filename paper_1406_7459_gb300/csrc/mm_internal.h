@@ -48,6 +48,7 @@ struct LlgCoef {
 };
 
 struct FastFns;
+struct FastSplitFns;
 
 // Launch shapes chosen at plan time.
 struct Launch {
@@ -58,6 +59,7 @@ struct Launch {
     const FastFns* fx = nullptr;     // compile-time x passes, if the grid has them
     const FastFns* fp = nullptr;     // compile-time plane kernel, if available
     bool split = false;              // pass 2 as y / z / y kernels (thick samples)
+    const FastSplitFns* fs2 = nullptr;  // compile-time split kernels, if the grid has them
 };
 
 enum Pass3Mode { kModeDemag = 0, kModeHeff = 1, kModeStep = 2 };
@@ -91,6 +93,18 @@ struct FastFns {
     int r3 = 0, t3 = 0;
     size_t s3 = 0;
 };
+// Compile-time split pass 2 (split_fast.cu): power-of-two ny in 16..1024,
+// nz in 8..128.
+struct FastSplitFns {
+    void (*yf)(Geom, float2*) = nullptr;
+    void (*yi)(Geom, float2*) = nullptr;
+    void (*zc)(Geom, float2*) = nullptr;
+    int ylpc = 0, ty = 0, zw = 0, tz = 0;
+    size_t sy = 0, sz = 0;
+};
+bool fast_split_lookup(int ny, int nz, FastSplitFns* f);
+cudaError_t configure_fast_split(const FastSplitFns& f);
+cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, float2* S, cudaStream_t s);
 bool fast_lookup_x(int nx, FastFns* f);
 bool fast_lookup_plane_nz1(int ny, FastFns* f);
 bool fast_lookup_plane_nz2(int ny, FastFns* f);

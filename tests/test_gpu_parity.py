@@ -377,12 +377,14 @@ def test_steps_interleaved_with_other_calls(grid):
     assert rel_l2(_host(out, grid), ref) < 1e-6
 
 
-THICK_GRIDS = [(8, 8, 9), (20, 12, 10), (16, 16, 16), (32, 32, 32), (24, 10, 12)]
+THICK_GRIDS = [(8, 8, 9), (20, 12, 10), (16, 16, 16), (32, 32, 32), (24, 10, 12), (16, 32, 64), (32, 16, 128),
+               (16, 512, 8)]
 
 
 @pytest.mark.parametrize("grid", THICK_GRIDS)
 def test_thick_samples_split_pass(grid):
-    """nz > 8: pass 2 runs as separate y / z / y kernels."""
+    """nz > 8, or a kx plane too large for shared memory: pass 2 runs as
+    separate y / z / y kernels (compile-time ones for power-of-two ny, nz)."""
     cell = (4e-9, 4e-9, 4e-9)
     M = inputs.random_unit_m(grid, MS, seed=51)
     ctx = _ctx(grid, cell, Ku=1e4, alpha=0.3)
