@@ -6,7 +6,8 @@ namespace mmk {
 
 template <int N>
 static void fill_xstep(FastStepFns* f) {
-    constexpr int R = kStepRows;
+    // four-row tiles where their shared memory fits comfortably, else two
+    constexpr int R = XstepLayout<N, kStepRows>::BYTES <= 200 * 1024 ? kStepRows : 2;
     f->kb = k_xstep_pdl<N, R>;
     f->rb = R;
     f->tb = XstepLayout<N, R>::THREADS;
