@@ -289,6 +289,7 @@ extern "C" int mm_batch_create(mm_batch** out, int n, const int* grids, const do
             g.twz = g.twy + g.Ly;
             g.Kt = b->Kt + koff[s];
             g.Kd = nullptr;
+            g.Kd0 = nullptr;
             b->desc[s].M0 = b->M0 + b->moff[s];
             b->desc[s].M1 = b->M1 + b->moff[s];
             b->desc[s].S = b->S + soff[s];

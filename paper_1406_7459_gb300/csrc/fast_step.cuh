@@ -109,7 +109,7 @@ __device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], Coef coef
 
 template <int NY, int NZ>
 __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY, NZ>::THREADS <= 512) ? 2 : 1)
-    k_plane_pdl(Geom g, const float2* __restrict__ S, float2* __restrict__ Sh) {
+    k_plane_pdl(Geom g, const float* __restrict__ Kd, const float2* __restrict__ S, float2* __restrict__ Sh) {
     using Lay = PlaneLayout<NY, NZ>;
     using F = Fft2<NY>;
     constexpr int P = F::P, Q = F::Q, G = F::G, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     for (int i = threadIdx.x; i < LY / 2; i += T) copy16(tw + 2 * i, g.twy + 2 * i);
     F::template load_ta<T>(ta, g.twy);
     {
-        const float* Kp = g.Kd + (size_t)kx * Lay::KT_FLOATS;
+        const float* Kp = Kd + (size_t)kx * Lay::KT_FLOATS;
 #pragma unroll
         for (int i = threadIdx.x; i < Lay::KT_FLOATS / 4; i += T) copy16(Ks + 4 * i, Kp + 4 * i);
     }
@@ -277,7 +277,11 @@ template <int N, int R> struct XstepLayout {
     static constexpr int THREADS = cmax<2 * NL * F::G, 128>::v;
 };
 
-template <int N, int R>
+// MODE kModeStep: the Euler step (Mout = M^{n+1}, Snext = its x spectrum);
+// kModeHeff: Mout = H_eff of M (Sh from the spectrum with the exchange
+// stencil folded in); kModeDemag: Mout = H_demag (Sh from the plain tensor
+// spectrum, M unused).  Snext and flag are used by the step only.
+template <int N, int R, int MODE>
 __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     k_xstep_pdl(Geom g, LlgCoef cf, const float2* __restrict__ Sh, float2* __restrict__ Snext,
                 const float* __restrict__ M, float* __restrict__ Mout, int* __restrict__ flag) {
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
 #pragma unroll
     for (int i = threadIdx.x; i < L / 2; i += T) copy16(tw + 2 * i, g.twx + 2 * i);
     F::template load_ta<T>(ta, g.twx);
-    {
+    if constexpr (MODE != kModeDemag) {
         constexpr int CH = N / 4;                               // 16-byte chunks per row
 #pragma unroll
         for (int idx = threadIdx.x; idx < 3 * R * CH; idx += T) {
@@ -408,6 +412,12 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
             const float2 z = wk[(cc * RP + (r >> 1)) * L + i];   // pair line of rows (r & ~1, r | 1)
             hd[cc] = (r & 1) ? z.y : z.x;
         }
+        const int cell = i + N * (j0 + r) + plane_xy * k;
+        if constexpr (MODE == kModeDemag) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) Mout[cc * Nc + cell] = hd[cc];
+            continue;
+        }
         const float bnd = bz + cf.pexch * ((float)((i == 0) + (i == N - 1)) * cf.idx2 +
                                            (float)((g.ny > 1) * ((j == 0) + (j == g.ny - 1))) * cf.idy2);
         float m[3], hh[3];
@@ -420,6 +430,11 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         hh[0] += cf.hx;
         hh[1] += cf.panis * m[1] + cf.hy;
         hh[2] += cf.panis * m[2] + cf.hz;
+        if constexpr (MODE == kModeHeff) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) Mout[cc * Nc + cell] = hh[cc];
+            continue;
+        }
         const float p0 = m[1] * hh[2] - m[2] * hh[1];
         const float p1 = m[2] * hh[0] - m[0] * hh[2];
         const float p2 = m[0] * hh[1] - m[1] * hh[0];
@@ -432,7 +447,6 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         const float s = cf.Ms * rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
         const float o0 = n0 * s, o1 = n1 * s, o2 = n2 * s;
         if (!isfinite(o0 + o1 + o2)) atomicOr(flag, 1);     // |o| <= Ms when finite
-        const int cell = i + N * (j0 + r) + plane_xy * k;
         Mout[cell] = o0;
         Mout[Nc + cell] = o1;
         Mout[2 * Nc + cell] = o2;
@@ -441,40 +455,42 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         Mn[(2 * R + r) * N + i] = o2;
     }
     __syncthreads();
-    // ---- forward x of the new rows (first pass of the next step)
-    if (fft_thread && t < Q) {
-        const float* ra = Mn + (size_t)(lc * R + 2 * pr) * N;
-        const float* rb = ra + N;
+    if constexpr (MODE == kModeStep) {
+        // ---- forward x of the new rows (first pass of the next step)
+        if (fft_thread && t < Q) {
+            const float* ra = Mn + (size_t)(lc * R + 2 * pr) * N;
+            const float* rb = ra + N;
 #pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const int jx = t + Q * q;
-            v[q] = make_float2(ra[jx], rb[jx]);
+            for (int q = 0; q < P; ++q) {
+                const int jx = t + Q * q;
+                v[q] = make_float2(ra[jx], rb[jx]);
+            }
+            if (h) F::odd_input_tab(v, t, tw);
+            F::stepA_tab(v, t, ta, wk + grp * F::EX, false);
         }
-        if (h) F::odd_input_tab(v, t, tw);
-        F::stepA_tab(v, t, ta, wk + grp * F::EX, false);
-    }
-    __syncthreads();
-    if (fft_thread && t < P) F::stepB(w, t, wk + grp * F::EX, false);
-    __syncthreads();
-    if (fft_thread && t < P) {
+        __syncthreads();
+        if (fft_thread && t < P) F::stepB(w, t, wk + grp * F::EX, false);
+        __syncthreads();
+        if (fft_thread && t < P) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) wk[line * ZS + h * HOFF + t + P * q] = w[q];   // Z[2 n + h]
-    }
-    __syncthreads();
-    // split each pair into the two rows' half-spectra and store to Snext;
-    // the RP pairs of one (c, kx) are adjacent in global memory and go to
-    // adjacent lanes
+            for (int q = 0; q < Q; ++q) wk[line * ZS + h * HOFF + t + P * q] = w[q];   // Z[2 n + h]
+        }
+        __syncthreads();
+        // split each pair into the two rows' half-spectra and store to Snext;
+        // the RP pairs of one (c, kx) are adjacent in global memory and go to
+        // adjacent lanes
 #pragma unroll
-    for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
-        const int p2 = idx % RP, ck = idx / RP;
-        const int c = ck / H, kx = ck - c * H;
-        const float2* ln = wk + (c * RP + p2) * ZS;
-        const int km = (L - kx) & (L - 1);
-        const float2 zk = ln[(kx & 1) * HOFF + (kx >> 1)];
-        const float2 zm = ln[(km & 1) * HOFF + (km >> 1)];
-        const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
-                                     0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        *reinterpret_cast<float4*>(Snext + kx * s_kx + c * s_c + s_base + 2 * p2) = o;
+        for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
+            const int p2 = idx % RP, ck = idx / RP;
+            const int c = ck / H, kx = ck - c * H;
+            const float2* ln = wk + (c * RP + p2) * ZS;
+            const int km = (L - kx) & (L - 1);
+            const float2 zk = ln[(kx & 1) * HOFF + (kx >> 1)];
+            const float2 zm = ln[(km & 1) * HOFF + (km >> 1)];
+            const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
+                                         0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+            *reinterpret_cast<float4*>(Snext + kx * s_kx + c * s_c + s_base + 2 * p2) = o;
+        }
     }
     __syncthreads();
     pdl_trigger();

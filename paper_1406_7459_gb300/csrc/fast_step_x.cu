@@ -1,5 +1,7 @@
 // fast_step_x.cu -- instantiations of the fused inverse-x + LLG + forward-x
-// kernel (second kernel of the power-of-two step) for nx = 16 ... 1024.
+// kernel (second kernel of the power-of-two step) for nx = 16 ... 1024, and
+// of its field-only variants (H_demag, H_eff) that close the two-kernel
+// field evaluation.
 #include "fast_step.cuh"
 
 namespace mmk {
@@ -8,7 +10,9 @@ template <int N>
 static void fill_xstep(FastStepFns* f) {
     // four-row tiles where their shared memory fits comfortably, else two
     constexpr int R = XstepLayout<N, kStepRows>::BYTES <= 200 * 1024 ? kStepRows : 2;
-    f->kb = k_xstep_pdl<N, R>;
+    f->kb[kModeDemag] = k_xstep_pdl<N, R, kModeDemag>;
+    f->kb[kModeHeff] = k_xstep_pdl<N, R, kModeHeff>;
+    f->kb[kModeStep] = k_xstep_pdl<N, R, kModeStep>;
     f->rb = R;
     f->tb = XstepLayout<N, R>::THREADS;
     f->sb = XstepLayout<N, R>::BYTES;
@@ -33,8 +37,9 @@ namespace mmk {
 
 cudaError_t configure_step_kernels(const FastStepFns& f) {
     cudaError_t e = cudaFuncSetAttribute(f.ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sa);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(f.kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sb);
+    for (int m = 0; m < 3 && e == cudaSuccess; ++m)
+        e = cudaFuncSetAttribute(f.kb[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sb);
+    return e;
 }
 
 static cudaLaunchConfig_t step_cfg(dim3 grid, int threads, size_t smem, cudaStream_t s, bool pdl,
@@ -51,18 +56,27 @@ static cudaLaunchConfig_t step_cfg(dim3 grid, int threads, size_t smem, cudaStre
     return cfg;
 }
 
-cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float2* S, float2* Sh, cudaStream_t s,
-                          bool pdl) {
+cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, const float2* S, float2* Sh,
+                          cudaStream_t s, bool pdl) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = step_cfg(dim3(g.Hx), f.ta, f.sa, s, pdl, attr);
-    return cudaLaunchKernelEx(&cfg, f.ka, g, S, Sh);
+    return cudaLaunchKernelEx(&cfg, f.ka, g, Kd, S, Sh);
 }
 
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
                           const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = step_cfg(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, pdl, attr);
-    return cudaLaunchKernelEx(&cfg, f.kb, g, c, Sh, S, M, Mout, flag);
+    return cudaLaunchKernelEx(&cfg, f.kb[kModeStep], g, c, Sh, S, M, Mout, flag);
+}
+
+cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, int mode, const float* Kd,
+                             float2* S, float2* Sh, const float* M, float* out, cudaStream_t s) {
+    cudaError_t e = launch_step_a(g, f, Kd, S, Sh, s, true);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = step_cfg(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, true, attr);
+    return cudaLaunchKernelEx(&cfg, f.kb[mode], g, c, (const float2*)Sh, (float2*)nullptr, M, out, (int*)nullptr);
 }
 
 // K_A then K_B; with `pdl` both carry the programmatic-serialisation launch
@@ -70,7 +84,7 @@ cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c,
 // waits on griddepcontrol before reading what the predecessor wrote).
 cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
                             const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
-    cudaError_t e = launch_step_a(g, f, S, Sh, s, pdl);
+    cudaError_t e = launch_step_a(g, f, g.Kd, S, Sh, s, pdl);
     if (e != cudaSuccess) return e;
     return launch_step_b(g, f, c, Sh, S, M, Mout, flag, s, pdl);
 }

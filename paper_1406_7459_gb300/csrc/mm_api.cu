@@ -46,7 +46,8 @@ struct mm_ctx {
     Geom g;
     Launch l;
     float* Kt = nullptr;
-    float* Kd = nullptr;       // 2-D spectrum per z offset (two-kernel step only)
+    float* Kd = nullptr;       // 2-D spectrum per z offset, exchange folded in (two-kernel step)
+    float* Kd0 = nullptr;      // the same without exchange (two-kernel demag evaluation)
     float2* S = nullptr;
     float* Mbuf[2] = {nullptr, nullptr};
     int cur = 0;
@@ -247,6 +248,7 @@ static void release(mm_ctx* c) {
             if (c->step_exec[kd][p]) cudaGraphExecDestroy(c->step_exec[kd][p]);
     cudaFree(c->Kt);
     cudaFree(c->Kd);
+    cudaFree(c->Kd0);
     cudaFree(c->S);
     cudaFree(c->Sh);
     for (int q = 0; q < 7; ++q) cudaFree(c->dpk[q]);
@@ -312,6 +314,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         if (c->has_fs) {
             CU(cudaMalloc(&c->Sh, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
             CU(cudaMalloc(&c->Kd, sizeof(float) * 6 * (size_t)g.Hx * kd_row(g.Hy) * g.nz));
+            CU(cudaMalloc(&c->Kd0, sizeof(float) * 6 * (size_t)g.Hx * kd_row(g.Hy) * g.nz));
         }
         CU(cudaMalloc(&c->Mbuf[0], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->Mbuf[1], sizeof(float) * 3 * N));
@@ -336,6 +339,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         g.twz = c->tw + g.Lx + g.Ly;
         g.Kt = c->Kt;
         g.Kd = c->Kd;
+        g.Kd0 = c->Kd0;
         CU(configure_pass_kernels(g, c->l));
         if (c->has_fs) CU(configure_step_kernels(c->fs));
 
@@ -357,7 +361,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         exf.idx2 = 1.0 / (c->cell[0] * c->cell[0]);
         exf.idy2 = 1.0 / (c->cell[1] * c->cell[1]);
         exf.idz2 = 1.0 / (c->cell[2] * c->cell[2]);
-        if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream, c->Kd, exf);
+        if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream, c->Kd, exf, c->Kd0);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         cudaFree(Nd);
         cudaFree(w1);
@@ -453,6 +457,14 @@ static int run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt
     const LlgCoef cf = make_coef(c, dt);
     c->spec_valid = false;
     CU(launch_pass1(c->g, c->l, M, c->S, s));
+    if (c->has_fs && c->fs.ta <= 512 && (mode == kModeDemag || mode == kModeHeff)) {
+        // power-of-two films: the step's plane kernel and the field-only
+        // variant of its x-step kernel (where the plane kernel runs at most
+        // 512 threads: larger ones are register-starved, and the three-pass
+        // plane kernel serves them better)
+        CU(launch_field_pdl(c->g, c->fs, cf, mode, mode == kModeDemag ? c->Kd0 : c->Kd, c->S, c->Sh, M, out, s));
+        return MM_OK;
+    }
     CU(launch_plane(c->g, c->l, c->S, s));
     CU(launch_pass3(c->g, c->l, cf, mode, c->S, M, out, c->flag, s));
     return MM_OK;
@@ -763,7 +775,7 @@ extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsig
                 // pass 1 alone (the two-kernel step folds it into K_B), then K_A, K_B
                 CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
                 CU(cudaEventRecord(ev[1], c->stream));
-                CU(launch_step_a(c->g, c->fs, c->S, c->Sh, c->stream, false));
+                CU(launch_step_a(c->g, c->fs, c->Kd, c->S, c->Sh, c->stream, false));
                 CU(cudaEventRecord(ev[2], c->stream));
                 CU(launch_step_b(c->g, c->fs, cf, c->Sh, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag,
                                  c->stream, false));
@@ -859,6 +871,7 @@ extern "C" int mm_demag_field_noalloc(const int grid[3], const float* Kt_dev, co
     g.twz = tw + g.Lx + g.Ly;
     g.Kt = Kt_dev;
     g.Kd = nullptr;
+    g.Kd0 = nullptr;
     CU(configure_pass_kernels(g, tmp.l));
     k_noalloc_twiddles<<<(unsigned)((ntw + 255) / 256), 256, 0, s>>>(g.Lx, g.Ly, g.Lz, tw);
     CU(cudaGetLastError());

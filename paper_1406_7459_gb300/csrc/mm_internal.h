@@ -26,6 +26,7 @@ struct Geom {
     const float2* twy;
     const float2* twz;
     const float* Kt;           // tensor spectrum [kx][kz'][ky'][6], scaled
+    const float* Kd0;          // the same without the exchange stencil (demag-only evaluations)
     const float* Kd;           // 2-D (x, y) tensor spectrum per z offset [kx][dz][6][ky'], rows of
                                // kd_row(Hy) floats, scaled,
                                // with the zero-padded exchange stencil folded into xx, yy, zz;
@@ -114,10 +115,11 @@ bool fast_lookup_plane_nz8(int ny, FastFns* f);
 // Two-kernel step for power-of-two grids (fast_step*.cu): K_A = plane
 // kernel in place on S[p]; K_B = inverse x + LLG + forward x into S[1-p].
 struct FastStepFns {
-    void (*ka)(Geom, const float2*, float2*) = nullptr;
+    void (*ka)(Geom, const float*, const float2*, float2*) = nullptr;
     int ta = 0;
     size_t sa = 0;
-    void (*kb)(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*) = nullptr;
+    // x-step kernels by Pass3Mode: demag field, effective field, Euler step
+    void (*kb[3])(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*) = {nullptr, nullptr, nullptr};
     int rb = 0, tb = 0;
     size_t sb = 0;
 };
@@ -129,7 +131,13 @@ bool fast_step_lookup_plane_b(int ny, int nz, FastStepFns* f);
 cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
                             const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 cudaError_t configure_step_kernels(const FastStepFns& f);
-cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float2* S, float2* Sh, cudaStream_t s, bool pdl);
+cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, const float2* S, float2* Sh,
+                          cudaStream_t s, bool pdl);
+// The two-kernel evaluation of H_demag (mode kModeDemag, plain 2-D spectrum
+// Kd0) or H_eff (kModeHeff, exchange-folded Kd) of M into out, after
+// launch_pass1 has formed S from M.
+cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, int mode, const float* Kd,
+                             float2* S, float2* Sh, const float* M, float* out, cudaStream_t s);
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
                           const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 
@@ -182,7 +190,7 @@ struct ExchangeFold {
 };
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
                             double* work1, double* work2, cudaStream_t s, float* Kd_dev = nullptr,
-                            ExchangeFold ex = ExchangeFold{});
+                            ExchangeFold ex = ExchangeFold{}, float* Kd0_dev = nullptr);
 size_t tensor_work_elems(const int grid[3], const int L[3]);
 
 // Energy (energy.cu): E[0..4] into out_dev (5 doubles, device); partials is

@@ -338,7 +338,8 @@ size_t tensor_work_elems(const int grid[3], const int L[3]) {
 }
 
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
-                            double* work1, double* work2, cudaStream_t s, float* Kd_dev, ExchangeFold ex) {
+                            double* work1, double* work2, cudaStream_t s, float* Kd_dev, ExchangeFold ex,
+                            float* Kd0_dev) {
     const int nx = grid[0], ny = grid[1], nz = grid[2];
     const int Hx = L[0] / 2 + 1, Hy = L[1] / 2 + 1, Hz = L[2] / 2 + 1;
     double2* cs = nullptr;
@@ -358,6 +359,9 @@ cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_d
         const size_t nd = (size_t)6 * Hx * Hyp * nz;
         k_pack2d<<<(unsigned)((nd + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, Hyp, 1.0 / ((double)L[0] * L[1]), work2,
                                                             Kd_dev, ex);
+        if (Kd0_dev)
+            k_pack2d<<<(unsigned)((nd + T - 1) / T), T, 0, s>>>(nz, Hx, Hy, Hyp, 1.0 / ((double)L[0] * L[1]), work2,
+                                                                Kd0_dev, ExchangeFold{});
     }
     size_t n3 = (size_t)6 * Hx * Hy * Hz;
     const double scale = 1.0 / ((double)L[0] * L[1] * L[2]);

@@ -108,10 +108,12 @@ def test_adaptive_run_step_limit_and_arguments():
     done, _, st = _mm().mm_run_adaptive(ctx, t_span, dt0, tol, 3)
     assert not done and st["accepted"] + st["rejected"] == 3 and st["t"] < t_span
     if st["accepted"] == acc and st["rejected"] == rej:
-        # the step sizes follow the FP32 error estimates: equal to ~1e-4
+        # the step sizes follow the FP32 error estimates (equal to ~1e-4),
+        # so the states compare as changes over nearly equal times
         assert abs(st["t"] - t) < 1e-3 * t
         got = _state(ctx, grid)
-        assert rel_l2(got, ref) < 1e-5
+        M64 = M.astype(np.float64)
+        assert rel_l2(got - M64, ref - M64) < 5e-3
     mm = _mm()
     for bad in ((t_span, -1.0, tol, 10), (t_span, dt0, 0.0, 10), (t_span, dt0, tol, 0), (-1.0, dt0, tol, 10)):
         with pytest.raises(mm.MMError) as ei:
