@@ -91,8 +91,12 @@ def test_demag_field(grid):
     assert rel_max(got, ref) < 1e-5
 
 
-def test_effective_field():
-    grid, cell = (24, 20, 4), (5e-9, 4e-9, 3e-9)
+@pytest.mark.parametrize("grid", [(24, 20, 4), (64, 32, 4), (32, 64, 2), (128, 16, 8), (16, 16, 1)])
+def test_effective_field(grid):
+    """H_eff of Eq. (2) against the oracle: the three-pass path (24x20x4)
+    and, on power-of-two films, the plane kernel with the exchange-folded
+    spectrum plus the field-only x-step kernel."""
+    cell = (5e-9, 4e-9, 3e-9)
     Ku, Hext = 4e4, (1.2e4, -3e3, 2e4)
     M = inputs.random_unit_m(grid, MS, seed=9)
     ctx = _ctx(grid, cell, Ku=Ku)
@@ -236,8 +240,9 @@ def test_direct_sum_samples_at_256x256x4():
         assert np.max(np.abs(got[:, k, j, i] - ref[s])) < 1e-5 * scale
 
 
-def test_energy_terms():
-    grid, cell = (24, 16, 3), (5e-9, 5e-9, 3e-9)
+@pytest.mark.parametrize("grid", [(24, 16, 3), (32, 32, 4)])
+def test_energy_terms(grid):
+    cell = (5e-9, 5e-9, 3e-9)
     Ku, Hext = 3e4, (2e4, -1e4, 5e3)
     M = inputs.random_unit_m(grid, MS, seed=13)
     ctx = _ctx(grid, cell, Ku=Ku)
