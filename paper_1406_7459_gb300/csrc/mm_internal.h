@@ -113,7 +113,9 @@ bool fast_lookup_plane_nz4(int ny, FastFns* f);
 bool fast_lookup_plane_nz8(int ny, FastFns* f);
 
 // Two-kernel step for power-of-two grids (fast_step*.cu): K_A = plane
-// kernel in place on S[p]; K_B = inverse x + LLG + forward x into S[1-p].
+// kernel from S into Sh (2-D spectrum given per launch: exchange-folded for
+// the step and H_eff, plain for H_demag); K_B = inverse x + LLG + forward x
+// from Sh into S, or its field-only variants.
 struct FastStepFns {
     void (*ka)(Geom, const float*, const float2*, float2*) = nullptr;
     int ta = 0;
