@@ -63,8 +63,6 @@ template <int NY, int NZ> struct PlaneLayout {
     static constexpr int TW_OFF = 0, TA_OFF = LY, KT_OFF = LY + NY, WORK_OFF = KT_OFF + ((KT_C + 1) / 2) * 2;
     static constexpr size_t BYTES = sizeof(float2) * (WORK_OFF + WORK);
     static constexpr int THREADS = 2 * NL * F::G;
-    static constexpr int ZTASKS = 3 * LY;                 // (ky column, output component)
-    static constexpr int ZTPT = (ZTASKS + THREADS - 1) / THREADS;
 };
 
 // Direct z sum of one (kx, ky) column for output component a, with
