@@ -182,6 +182,22 @@ def max_over_ranks(v, ws):
     return float(t.item())
 
 
+def sum_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(n, rank, ws):
+    """Round-robin share of n independent samples for one rank (the samples
+    are of uneven size; interleaving balances the ranks' cell counts)."""
+    return list(range(rank, n, ws))
+
+
 def oracle_rate(seconds_budget=15.0, max_steps=None):
     """Time the FP64 numpy oracle's Euler step on the same workload, on a
     bounded number of steps; returns (cells*steps/s, steps, seconds)."""
@@ -427,11 +443,14 @@ def run_batch(args, rank, ws):
     """512 independent samples of uneven size (nx 16..256, ny 16..64,
     nz 1..2, random Ku, H_ext, alpha) stepped as one batch after the tile
     autotuner, against the same samples stepped one context at a time.  The
-    batch working set (~0.7 GB) exceeds L2, so steps run back to back."""
+    batch working set (~0.7 GB) exceeds L2, so steps run back to back.
+    Under torchrun each rank takes a round-robin share of the samples (no
+    data-path collective; the ranks' cell counts are summed and their
+    times max-reduced on the host)."""
     import torch
     from paper_1406_7459_gb300 import mm, inputs
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    samples = inputs.batch_samples(512, seed=3)
+    samples = [inputs.batch_samples(512, seed=3)[i] for i in shard(512, rank, ws)]
     dt = 5e-14
     b = mm.mm_batch_create([s["grid"] for s in samples], [s["cell"] for s in samples],
                            [s["Ms"] for s in samples], [s["A"] for s in samples], [s["Ku"] for s in samples],
@@ -443,14 +462,17 @@ def run_batch(args, rank, ws):
     cells = mm.mm_batch_cells(b)
     K = max(10, min(args.steps, 200))
     mm.mm_batch_step(b, max(args.warmup, 3), dt)
+    barrier(ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     mm.mm_batch_step(b, K, dt)
     e1.record()
     torch.cuda.synchronize()
+    barrier(ws)
     mm.mm_batch_sync(b)
-    batch_ms = e0.elapsed_time(e1) / K
+    batch_ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+    cells = int(sum_over_ranks(float(cells), ws))
     # the same samples, one context each, stepped one after another
     ctxs = []
     for s in samples:
@@ -467,13 +489,14 @@ def run_batch(args, rank, ws):
             mm.mm_step(c, 1, dt)
     e1.record()
     torch.cuda.synchronize()
-    single_ms = e0.elapsed_time(e1) / Ks
+    single_ms = max_over_ranks(e0.elapsed_time(e1) / Ks, ws)
     for c in ctxs:
         mm.mm_destroy(c)
     if rank == 0:
         print(json.dumps({"workload": "batch of 512 samples, nx 16..256, ny 16..64, nz 1..2, Ku U[0,1e4], "
                                       "|H_ext| U[0,5e4] random direction, alpha U[0.01,0.5], Euler dt 5e-14 s",
                           "metric": "cells*steps/s over the batch", "dtype": "f32", "data": "synthetic",
+                          "n_gpus": ws, "sharding": "round-robin samples per rank, no data-path collective",
                           "cells": cells, "batched_ms_per_step": batch_ms,
                           "batched_cells_steps_per_s": cells / (batch_ms * 1e-3),
                           "one_context_at_a_time_ms_per_step": single_ms,
