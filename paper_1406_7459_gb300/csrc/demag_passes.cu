@@ -19,6 +19,7 @@ namespace mmk {
 
 __global__ void __launch_bounds__(256) k_pass1(Geom g, int R, int group, const float* __restrict__ M,
                                                 float2* __restrict__ S) {
+    pdl_wait();
     pass1_body(g, R, group, M, S, blockIdx.x);
 }
 
@@ -26,6 +27,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_pass3(Geom g, int R, int group, LlgCoef cf,
                                                 const float2* __restrict__ S, const float* __restrict__ M,
                                                 float* __restrict__ out, int* __restrict__ flag) {
+    pdl_wait();
     pass3_body<MODE>(g, R, group, cf, S, M, out, flag, blockIdx.x);
 }
 
@@ -63,9 +65,9 @@ cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
     return cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem2);
 }
 
-// Launch configuration with programmatic serialisation: the compile-time
-// pass kernels wait on griddepcontrol before touching M, S or their output,
-// so each may start while the previous kernel on the stream drains.
+// Launch configuration with programmatic serialisation: every pass kernel
+// waits on griddepcontrol before touching M, S or its output, so each may
+// start while the previous kernel on the stream drains.
 static cudaLaunchConfig_t pdl_cfg(int grid, int threads, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -86,8 +88,9 @@ cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2*
         return cudaLaunchKernelEx(&cfg, l.fx->p1, g, M, S);
     }
     const int ntj = (g.ny + l.r1 - 1) / l.r1;
-    k_pass1<<<3 * g.nz * ntj, l.t1, l.smem1, s>>>(g, l.r1, l.g1, M, S);
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_cfg(3 * g.nz * ntj, l.t1, l.smem1, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_pass1, g, l.r1, l.g1, M, S);
 }
 
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s) {
@@ -100,8 +103,9 @@ cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t
     }
     PlaneFn pf = plane_fn(g.Lz);
     if (!pf) return cudaErrorInvalidValue;
-    pf<<<g.Hx, l.t2, l.smem2, s>>>(g, l.g2, S);
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_cfg(g.Hx, l.t2, l.smem2, s, attr);
+    return cudaLaunchKernelEx(&cfg, pf, g, l.g2, S);
 }
 
 cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int mode, const float2* S,
@@ -112,13 +116,13 @@ cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int m
         return cudaLaunchKernelEx(&cfg, l.fx->p3[mode], g, c, S, M, out, flag);
     }
     const int ntj = (g.ny + l.r3 - 1) / l.r3;
-    const int grid = g.nz * ntj;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_cfg(g.nz * ntj, l.t3, l.smem3, s, attr);
     switch (mode) {
-        case kModeDemag: k_pass3<kModeDemag><<<grid, l.t3, l.smem3, s>>>(g, l.r3, l.g3, c, S, M, out, flag); break;
-        case kModeHeff: k_pass3<kModeHeff><<<grid, l.t3, l.smem3, s>>>(g, l.r3, l.g3, c, S, M, out, flag); break;
-        default: k_pass3<kModeStep><<<grid, l.t3, l.smem3, s>>>(g, l.r3, l.g3, c, S, M, out, flag); break;
+        case kModeDemag: return cudaLaunchKernelEx(&cfg, k_pass3<kModeDemag>, g, l.r3, l.g3, c, S, M, out, flag);
+        case kModeHeff: return cudaLaunchKernelEx(&cfg, k_pass3<kModeHeff>, g, l.r3, l.g3, c, S, M, out, flag);
+        default: return cudaLaunchKernelEx(&cfg, k_pass3<kModeStep>, g, l.r3, l.g3, c, S, M, out, flag);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace mmk

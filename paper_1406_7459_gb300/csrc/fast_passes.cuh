@@ -16,13 +16,6 @@
 
 namespace mmk {
 
-// Programmatic dependent launch: a kernel launched with the programmatic-
-// serialisation attribute may start while its predecessor drains; it must
-// call pdl_wait() before it reads or writes anything the predecessor may
-// touch.  pdl_trigger() lets the successor launch early.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 // shared-memory padding of a spectrum line: one slot every 16
 __device__ __forceinline__ int pz(int k) { return k + (k >> 4); }
 __host__ __device__ constexpr int pzlen(int L) { return L + L / 16 + 1; }

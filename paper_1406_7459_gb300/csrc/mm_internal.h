@@ -33,6 +33,16 @@ struct Geom {
                                // used by the direct-z plane kernel of the power-of-two step
 };
 
+#ifdef __CUDACC__
+// Programmatic dependent launch: a kernel launched with the programmatic-
+// serialisation attribute may start while its predecessor drains; it must
+// call pdl_wait() before it reads or writes anything the predecessor may
+// touch (a no-op when launched without the attribute).  pdl_trigger() lets
+// the successor launch early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
 // Row length (floats) of the 2-D spectrum Kd: Hy rounded up to 16 bytes.
 inline __host__ __device__ constexpr int kd_row(int Hy) { return (Hy + 3) & ~3; }
 

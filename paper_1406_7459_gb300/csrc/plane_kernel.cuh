@@ -104,6 +104,7 @@ __device__ __forceinline__ void plane_body(const Geom& g, int group, float2* __r
 
 template <int LZ>
 __global__ void __launch_bounds__(512) k_plane(Geom g, int group, float2* __restrict__ S) {
+    pdl_wait();
     plane_body<LZ>(g, group, S, blockIdx.x);
 }
 

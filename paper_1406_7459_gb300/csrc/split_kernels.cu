@@ -15,6 +15,7 @@ namespace mmk {
 
 __global__ void __launch_bounds__(256) k_yfft(Geom g, int lines_per_cta, int inverse, float2* __restrict__ S) {
     extern __shared__ float2 sm[];
+    pdl_wait();
     const int lstride = padded_len(g.Ly);
     const int total = g.Hx * 3 * g.nz;
     const int l0 = blockIdx.x * lines_per_cta;
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(256) k_yfft(Geom g, int lines_per_cta, int inv
 
 __global__ void __launch_bounds__(256) k_zconv(Geom g, int W, float2* __restrict__ S) {
     extern __shared__ float2 sm[];
+    pdl_wait();
     const int nchunk = (g.Ly + W - 1) / W;
     const int kx = blockIdx.x / nchunk;
     const int ky0 = (blockIdx.x % nchunk) * W;
@@ -108,16 +110,27 @@ cudaError_t launch_split_plane(const Geom& g, float2* S, cudaStream_t s) {
     const int lp = split_lines_per_cta(g);
     const int total = g.Hx * 3 * g.nz;
     const int gy = (total + lp - 1) / lp;
-    k_yfft<<<gy, 256, split_smem_y(g), s>>>(g, lp, 0, S);
-    cudaError_t e = cudaGetLastError();
+    // programmatic serialisation: both kernels wait on griddepcontrol first
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cy = {};
+    cy.gridDim = dim3(gy);
+    cy.blockDim = dim3(256);
+    cy.dynamicSmemBytes = split_smem_y(g);
+    cy.stream = s;
+    cy.attrs = attr;
+    cy.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cy, k_yfft, g, lp, 0, S);
     if (e != cudaSuccess) return e;
     const int W = split_chunk(g);
     const int nchunk = (g.Ly + W - 1) / W;
-    k_zconv<<<g.Hx * nchunk, 256, split_smem_z(g), s>>>(g, W, S);
-    e = cudaGetLastError();
+    cudaLaunchConfig_t cz = cy;
+    cz.gridDim = dim3(g.Hx * nchunk);
+    cz.dynamicSmemBytes = split_smem_z(g);
+    e = cudaLaunchKernelEx(&cz, k_zconv, g, W, S);
     if (e != cudaSuccess) return e;
-    k_yfft<<<gy, 256, split_smem_y(g), s>>>(g, lp, 1, S);
-    return cudaGetLastError();
+    return cudaLaunchKernelEx(&cy, k_yfft, g, lp, 1, S);
 }
 
 }  // namespace mmk
