@@ -105,7 +105,7 @@ struct FastFns {
     size_t s3 = 0;
 };
 // Compile-time split pass 2 (split_fast.cu): power-of-two ny in 16..1024,
-// nz in 8..128.
+// nz in 1..128 (zw = 0: one y position per thread for nz <= 8).
 struct FastSplitFns {
     void (*yf)(Geom, float2*) = nullptr;
     void (*yi)(Geom, float2*) = nullptr;

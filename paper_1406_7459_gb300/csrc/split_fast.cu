@@ -1,7 +1,7 @@
 // split_fast.cu -- pass 2 for thick power-of-two samples with compile-time
 // FFTs: the y transforms and the z transform + tensor product of Sec. 3
 // (Eqs. (14)-(16)) as three kernels on the spectrum workspace (row stride
-// Ly), for ny in 16 ... 1024 and nz in 8 ... 128.
+// Ly), for ny in 16 ... 1024 and nz in 1, 2, 4, 8 ... 128.
 //
 //   k_yfwd_fast<NY>  per batch of (kx, c, k) lines: forward y of the ny
 //                    nonzero inputs as the two unpadded halves of the padded
@@ -205,6 +205,33 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS) k_zconv_fast(Geom g, flo
     }
 }
 
+// Thin z (nz <= 8): one y position per thread, its 3 nz values held in
+// registers through the z transform, the product and the inverse
+// (zconv_column); consecutive threads take consecutive positions, so every
+// (c, k) row is read and written coalesced, and no barrier is needed.
+constexpr int kZcolThreads = 128;
+
+template <int NZ>
+__global__ void __launch_bounds__(kZcolThreads) k_zcol_fast(Geom g, float2* __restrict__ S) {
+    pdl_wait();
+    const int p = blockIdx.x * kZcolThreads + threadIdx.x;      // y position within the kx plane
+    const int kx = blockIdx.y;
+    if (p >= g.Ly) return;
+    const int NYh = g.Ly / 2;
+    const int ky = 2 * (p % NYh) + p / NYh;                      // the forward y kernel's order
+    float2* base = S + (size_t)kx * 3 * NZ * g.Jst + p;
+    float2 m[3][NZ];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) m[c][k] = base[(size_t)(c * NZ + k) * g.Jst];
+    zconv_column<NZ>(m, g.Kt + (size_t)kx * g.Hz * g.Hy * 6, g.Hy, g.Ly, ky, g.twz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) base[(size_t)(c * NZ + k) * g.Jst] = m[c][k];
+}
+
 template <int NY> static void fill_y(FastSplitFns* f) {
     f->yf = k_yfwd_fast<NY>;
     f->yi = k_yinv_fast<NY>;
@@ -217,6 +244,12 @@ template <int NZ> static void fill_z(FastSplitFns* f) {
     f->zw = ZLayout<NZ>::W;
     f->tz = ZLayout<NZ>::THREADS;
     f->sz = ZLayout<NZ>::BYTES;
+}
+template <int NZ> static void fill_zcol(FastSplitFns* f) {
+    f->zc = k_zcol_fast<NZ>;
+    f->zw = 0;                               // marks the one-position-per-thread kernel
+    f->tz = kZcolThreads;
+    f->sz = 0;
 }
 
 bool fast_split_lookup(int ny, int nz, FastSplitFns* f) {
@@ -231,7 +264,10 @@ bool fast_split_lookup(int ny, int nz, FastSplitFns* f) {
         default: return false;
     }
     switch (nz) {
-        case 8: fill_z<8>(f); break;
+        case 1: fill_zcol<1>(f); break;
+        case 2: fill_zcol<2>(f); break;
+        case 4: fill_zcol<4>(f); break;
+        case 8: fill_zcol<8>(f); break;
         case 16: fill_z<16>(f); break;
         case 32: fill_z<32>(f); break;
         case 64: fill_z<64>(f); break;
@@ -244,7 +280,7 @@ bool fast_split_lookup(int ny, int nz, FastSplitFns* f) {
 cudaError_t configure_fast_split(const FastSplitFns& f) {
     cudaError_t e = cudaFuncSetAttribute(f.yf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sy);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f.yi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sy);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f.zc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sz);
+    if (e == cudaSuccess && f.sz) e = cudaFuncSetAttribute(f.zc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sz);
     return e;
 }
 
@@ -268,7 +304,9 @@ cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, float2* S, c
     cudaLaunchConfig_t cy = split_cfg(gy, f.ty, f.sy, s, attr);
     cudaError_t e = cudaLaunchKernelEx(&cy, f.yf, g, S);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cz = split_cfg(g.Hx * (g.Ly / f.zw), f.tz, f.sz, s, attr);
+    cudaLaunchConfig_t cz = f.zw ? split_cfg(g.Hx * (g.Ly / f.zw), f.tz, f.sz, s, attr)
+                                 : split_cfg(1, f.tz, 0, s, attr);
+    if (!f.zw) cz.gridDim = dim3((g.Ly + f.tz - 1) / f.tz, g.Hx);
     e = cudaLaunchKernelEx(&cz, f.zc, g, S);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cy, f.yi, g, S);

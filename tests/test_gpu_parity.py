@@ -383,7 +383,7 @@ def test_steps_interleaved_with_other_calls(grid):
 
 
 THICK_GRIDS = [(8, 8, 9), (20, 12, 10), (16, 16, 16), (32, 32, 32), (24, 10, 12), (16, 32, 64), (32, 16, 128),
-               (16, 512, 8)]
+               (16, 512, 8), (16, 1024, 4)]
 
 
 @pytest.mark.parametrize("grid", THICK_GRIDS)
