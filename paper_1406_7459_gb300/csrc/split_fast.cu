@@ -109,11 +109,12 @@ template <int NZ> struct ZLayout {
     static constexpr int W = cmax_i(64 / F::G, 1);            // y positions per CTA (384 threads)
     static constexpr int THREADS = 6 * W * F::G;
     static constexpr int ZP = 2 * NZ + 1;                        // z-line stride in shared memory
+    static constexpr int MINB = NZ >= 128 ? 3 : 1;               // CTAs per SM the registers must allow
     static constexpr size_t BYTES = sizeof(float2) * (2 * NZ + 3 * W * ZP + 6 * W * F::EX);
 };
 
 template <int NZ>
-__global__ void __launch_bounds__(ZLayout<NZ>::THREADS) k_zconv_fast(Geom g, float2* __restrict__ S) {
+__global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zconv_fast(Geom g, float2* __restrict__ S) {
     using Lay = ZLayout<NZ>;
     using F = Fft2<NZ>;
     constexpr int P = F::P, Q = F::Q, G = F::G, T = Lay::THREADS, W = Lay::W, ZP = Lay::ZP;
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS) k_zconv_fast(Geom g, flo
     for (int i = threadIdx.x; i < 2 * NZ; i += T) tw[i] = __ldg(g.twz + i);
     pdl_wait();
     const float2* base = S + (size_t)kx * 3 * NZ * g.Jst + p0;
+#pragma unroll
     for (int idx = threadIdx.x; idx < 3 * NZ * W; idx += T) {
         const int w = idx % W, ck = idx / W;          // ck = c*NZ + k
         const int c = ck / NZ, k = ck % NZ;
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS) k_zconv_fast(Geom g, flo
     // tensor product per (y position, kz); the y position p holds
     // ky = 2 (p mod ny) + p / ny (the forward y kernel's order)
     const float* Kp = g.Kt + (size_t)kx * g.Hz * g.Hy * 6;
+#pragma unroll
     for (int idx = threadIdx.x; idx < W * 2 * NZ; idx += T) {
         const int w = idx % W, zp = idx / W;
         const int kz = 2 * (zp % NZ) + zp / NZ;
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS) k_zconv_fast(Geom g, flo
     }
     __syncthreads();
     float2* out = S + (size_t)kx * 3 * NZ * g.Jst + p0;
+#pragma unroll
     for (int idx = threadIdx.x; idx < 3 * NZ * W; idx += T) {
         const int w2 = idx % W, ck = idx / W;
         const int c = ck / NZ, k = ck % NZ;
