@@ -94,7 +94,7 @@ cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2*
 }
 
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s) {
-    if (l.split && l.fs2) return launch_fast_split(g, *l.fs2, S, s);
+    if (l.split && l.fs2) return launch_fast_split(g, *l.fs2, g.Kt, S, s);
     if (l.split) return launch_split_plane(g, S, s);
     if (l.fp) {
         cudaLaunchAttribute attr[1];

@@ -36,7 +36,8 @@ bool fast_step_lookup_x(int nx, FastStepFns* f) {
 namespace mmk {
 
 cudaError_t configure_step_kernels(const FastStepFns& f) {
-    cudaError_t e = cudaFuncSetAttribute(f.ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sa);
+    cudaError_t e = f.ka ? cudaFuncSetAttribute(f.ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sa)
+                         : cudaSuccess;                   // x-step only (thick samples)
     for (int m = 0; m < 3 && e == cudaSuccess; ++m)
         e = cudaFuncSetAttribute(f.kb[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.sb);
     return e;

@@ -66,6 +66,8 @@ struct mm_ctx {
     FastStepFns fs;            // two-kernel step (power-of-two grids)
     FastSplitFns fsplit;       // compile-time split pass 2 (thick power-of-two samples)
     bool has_fs = false;
+    bool has_ss = false;       // thick power-of-two samples: split pass 2 + the x-step kernel
+    float* Kt_ex = nullptr;    // tensor spectrum with the exchange stencil folded in (has_ss)
     float2* Sh = nullptr;      // plane-kernel output of the two-kernel step (layout of S)
     int method = MM_INTEGRATOR_EULER;
     float* Mst = nullptr;      // Runge-Kutta stage state
@@ -201,6 +203,11 @@ static int build_plan(mm_ctx* c) {
         // the x-step kernel indexes the spectrum and M with 32-bit offsets
         ok = ok && 3.0 * g.Hx * g.nz * g.Jst < (double)INT_MAX && 3.0 * g.N < (double)INT_MAX;
         c->has_fs = ok;
+        // thick samples: the compile-time split pass with the x-step kernel
+        // (same 32-bit offset limits)
+        c->has_ss = !ok && l.split && l.fs2 && s.kb[kModeStep] && g.ny % s.rb == 0 && s.sb <= smem_cap &&
+                    3.0 * g.Hx * g.nz * g.Jst < (double)INT_MAX && 3.0 * g.N < (double)INT_MAX;
+        if (c->has_ss) s.ka = nullptr;
     }
     return MM_OK;
 }
@@ -249,6 +256,7 @@ static void release(mm_ctx* c) {
     cudaFree(c->Kt);
     cudaFree(c->Kd);
     cudaFree(c->Kd0);
+    cudaFree(c->Kt_ex);
     cudaFree(c->S);
     cudaFree(c->Sh);
     for (int q = 0; q < 7; ++q) cudaFree(c->dpk[q]);
@@ -316,6 +324,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
             CU(cudaMalloc(&c->Kd, sizeof(float) * 6 * (size_t)g.Hx * kd_row(g.Hy) * g.nz));
             CU(cudaMalloc(&c->Kd0, sizeof(float) * 6 * (size_t)g.Hx * kd_row(g.Hy) * g.nz));
         }
+        if (c->has_ss) CU(cudaMalloc(&c->Kt_ex, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.Hz));
         CU(cudaMalloc(&c->Mbuf[0], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->Mbuf[1], sizeof(float) * 3 * N));
         CU(cudaMalloc(&c->H, sizeof(float) * 3 * N));
@@ -341,7 +350,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         g.Kd = c->Kd;
         g.Kd0 = c->Kd0;
         CU(configure_pass_kernels(g, c->l));
-        if (c->has_fs) CU(configure_step_kernels(c->fs));
+        if (c->has_fs || c->has_ss) CU(configure_step_kernels(c->fs));
 
         // tensor set-up in FP64
         const int L[3] = {g.Lx, g.Ly, g.Lz};
@@ -362,6 +371,11 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         exf.idy2 = 1.0 / (c->cell[1] * c->cell[1]);
         exf.idz2 = 1.0 / (c->cell[2] * c->cell[2]);
         if (e == cudaSuccess) e = tensor_spectrum(c->grid, L, Nd, c->Kt, w1, w2, c->stream, c->Kd, exf, c->Kd0);
+        if (e == cudaSuccess && c->has_ss) {
+            ExchangeFold ex3 = exf;
+            ex3.on = 1;
+            e = tensor_fold_exchange3(c->g, ex3, c->Kt, c->Kt_ex, c->stream);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         cudaFree(Nd);
         cudaFree(w1);
@@ -465,6 +479,11 @@ static int run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt
         CU(launch_field_pdl(c->g, c->fs, cf, mode, mode == kModeDemag ? c->Kd0 : c->Kd, c->S, c->Sh, M, out, s));
         return MM_OK;
     }
+    if (c->has_ss && (mode == kModeDemag || mode == kModeHeff)) {
+        CU(launch_split_xstep(c->g, c->fsplit, c->fs, cf, mode, mode == kModeDemag ? c->Kt : c->Kt_ex, c->S, M,
+                              out, nullptr, s));
+        return MM_OK;
+    }
     CU(launch_plane(c->g, c->l, c->S, s));
     CU(launch_pass3(c->g, c->l, cf, mode, c->S, M, out, c->flag, s));
     return MM_OK;
@@ -515,6 +534,11 @@ static int enqueue_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
                            c->flag, s, true));
         return MM_OK;
     }
+    if (c->has_ss) {
+        CU(launch_split_xstep(c->g, c->fsplit, c->fs, make_coef(c, dt), kModeStep, c->Kt_ex, c->S, c->Mbuf[p],
+                              c->Mbuf[1 - p], c->flag, s));
+        return MM_OK;
+    }
     return run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, s);
 }
 
@@ -552,7 +576,7 @@ static int capture_step(mm_ctx* c, int kind, int p, double dt) {
 
 // Form S[cur] from M[cur] when the two-kernel step needs it.
 static int ensure_spectrum(mm_ctx* c) {
-    if (!c->has_fs || c->spec_valid || c->method != MM_INTEGRATOR_EULER) return MM_OK;
+    if (!(c->has_fs || c->has_ss) || c->spec_valid || c->method != MM_INTEGRATOR_EULER) return MM_OK;
     CU(launch_pass1(c->g, c->l, c->Mbuf[c->cur], c->S, c->stream));
     c->spec_valid = true;
     return MM_OK;
@@ -733,7 +757,7 @@ extern "C" int mm_plan_info(const mm_ctx* c, int L[3]) {
         L[1] = c->g.Ly;
         L[2] = c->g.Lz;
     }
-    return c->has_fs ? 2 : (c->l.split ? 5 : 3);
+    return c->has_fs ? 2 : (c->has_ss ? 4 : (c->l.split ? 5 : 3));
 }
 
 extern "C" int mm_tensor_octant(mm_ctx* c, double* out) {
@@ -781,6 +805,7 @@ extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsig
                                  c->stream, false));
                 c->spec_valid = true;
             } else {
+                c->spec_valid = false;            // S no longer holds a step's x spectrum
                 CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
                 CU(cudaEventRecord(ev[1], c->stream));
                 CU(launch_plane(c->g, c->l, c->S, c->stream));

@@ -109,13 +109,16 @@ struct FastFns {
 struct FastSplitFns {
     void (*yf)(Geom, float2*) = nullptr;
     void (*yi)(Geom, float2*) = nullptr;
-    void (*zc)(Geom, float2*) = nullptr;
+    void (*zc)(Geom, const float*, float2*) = nullptr;
     int ylpc = 0, ty = 0, zw = 0, tz = 0;
     size_t sy = 0, sz = 0;
 };
 bool fast_split_lookup(int ny, int nz, FastSplitFns* f);
 cudaError_t configure_fast_split(const FastSplitFns& f);
-cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, float2* S, cudaStream_t s);
+// y forward, z transform + product with the tensor spectrum Kt (g.Kt, or
+// the exchange-folded copy for the split step), y inverse; in place on S.
+cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, const float* Kt, float2* S, cudaStream_t s);
+
 bool fast_lookup_x(int nx, FastFns* f);
 bool fast_lookup_plane_nz1(int ny, FastFns* f);
 bool fast_lookup_plane_nz2(int ny, FastFns* f);
@@ -150,6 +153,11 @@ cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, 
 // launch_pass1 has formed S from M.
 cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, int mode, const float* Kd,
                              float2* S, float2* Sh, const float* M, float* out, cudaStream_t s);
+// Thick-sample step / field: launch_fast_split with Kt, then the x-step
+// kernel of mode `mode` in place on S (S -> S, M -> out).
+cudaError_t launch_split_xstep(const Geom& g, const FastSplitFns& f2, const FastStepFns& fs, const LlgCoef& c,
+                               int mode, const float* Kt, float2* S, const float* M, float* out, int* flag,
+                               cudaStream_t s);
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
                           const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 
@@ -203,6 +211,9 @@ struct ExchangeFold {
 cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_dev, float* Kt_dev,
                             double* work1, double* work2, cudaStream_t s, float* Kd_dev = nullptr,
                             ExchangeFold ex = ExchangeFold{}, float* Kd0_dev = nullptr);
+// Kt_ex = Kt plus the zero-padded 7-point exchange stencil's symbol on the
+// diagonal (the 3-D counterpart of the fold into Kd).
+cudaError_t tensor_fold_exchange3(const Geom& g, ExchangeFold ex, const float* Kt, float* Kt_ex, cudaStream_t s);
 size_t tensor_work_elems(const int grid[3], const int L[3]);
 
 // Energy (energy.cu): E[0..4] into out_dev (5 doubles, device); partials is

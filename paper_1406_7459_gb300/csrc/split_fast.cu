@@ -114,7 +114,7 @@ template <int NZ> struct ZLayout {
 };
 
 template <int NZ>
-__global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zconv_fast(Geom g, float2* __restrict__ S) {
+__global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zconv_fast(Geom g, const float* __restrict__ Kt, float2* __restrict__ S) {
     using Lay = ZLayout<NZ>;
     using F = Fft2<NZ>;
     constexpr int P = F::P, Q = F::Q, G = F::G, T = Lay::THREADS, W = Lay::W, ZP = Lay::ZP;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zco
     __syncthreads();
     // tensor product per (y position, kz); the y position p holds
     // ky = 2 (p mod ny) + p / ny (the forward y kernel's order)
-    const float* Kp = g.Kt + (size_t)kx * g.Hz * g.Hy * 6;
+    const float* Kp = Kt + (size_t)kx * g.Hz * g.Hy * 6;
 #pragma unroll
     for (int idx = threadIdx.x; idx < W * 2 * NZ; idx += T) {
         const int w = idx % W, zp = idx / W;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zco
 constexpr int kZcolThreads = 128;
 
 template <int NZ>
-__global__ void __launch_bounds__(kZcolThreads) k_zcol_fast(Geom g, float2* __restrict__ S) {
+__global__ void __launch_bounds__(kZcolThreads) k_zcol_fast(Geom g, const float* __restrict__ Kt, float2* __restrict__ S) {
     pdl_wait();
     const int p = blockIdx.x * kZcolThreads + threadIdx.x;      // y position within the kx plane
     const int kx = blockIdx.y;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kZcolThreads) k_zcol_fast(Geom g, float2* __re
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int k = 0; k < NZ; ++k) m[c][k] = base[(size_t)(c * NZ + k) * g.Jst];
-    zconv_column<NZ>(m, g.Kt + (size_t)kx * g.Hz * g.Hy * 6, g.Hy, g.Ly, ky, g.twz);
+    zconv_column<NZ>(m, Kt + (size_t)kx * g.Hz * g.Hy * 6, g.Hy, g.Ly, ky, g.twz);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -301,7 +301,7 @@ static cudaLaunchConfig_t split_cfg(int grid, int threads, size_t smem, cudaStre
     return cfg;
 }
 
-cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, float2* S, cudaStream_t s) {
+cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, const float* Kt, float2* S, cudaStream_t s) {
     cudaLaunchAttribute attr[1];
     const int lines = g.Hx * 3 * g.nz;
     const int gy = (lines + f.ylpc - 1) / f.ylpc;
@@ -311,9 +311,22 @@ cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, float2* S, c
     cudaLaunchConfig_t cz = f.zw ? split_cfg(g.Hx * (g.Ly / f.zw), f.tz, f.sz, s, attr)
                                  : split_cfg(1, f.tz, 0, s, attr);
     if (!f.zw) cz.gridDim = dim3((g.Ly + f.tz - 1) / f.tz, g.Hx);
-    e = cudaLaunchKernelEx(&cz, f.zc, g, S);
+    e = cudaLaunchKernelEx(&cz, f.zc, g, Kt, S);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cy, f.yi, g, S);
+}
+
+cudaError_t launch_split_xstep(const Geom& g, const FastSplitFns& f2, const FastStepFns& fs, const LlgCoef& c,
+                               int mode, const float* Kt, float2* S, const float* M, float* out, int* flag,
+                               cudaStream_t s) {
+    cudaError_t e = launch_fast_split(g, f2, Kt, S, s);
+    if (e != cudaSuccess) return e;
+    // the x-step kernel reads its tile of S (all kx of R rows of a layer)
+    // into shared memory before it writes the same tile back: in place
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = split_cfg(g.nz * (g.ny / fs.rb), fs.tb, fs.sb, s, attr);
+    return cudaLaunchKernelEx(&cfg, fs.kb[mode], g, c, (const float2*)S, mode == kModeStep ? S : (float2*)nullptr,
+                              M, out, mode == kModeStep ? flag : (int*)nullptr);
 }
 
 }  // namespace mmk

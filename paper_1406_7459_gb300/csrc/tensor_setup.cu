@@ -371,4 +371,33 @@ cudaError_t tensor_spectrum(const int grid[3], const int L[3], const double* N_d
     return e != cudaSuccess ? e : e2;
 }
 
+// Kt_ex = Kt + the symbol of the zero-padded 7-point exchange stencil of
+// Eq. (4) on xx, yy, zz (axes of one cell skipped), in the stored scaling
+// 1/(Lx Ly Lz).  The update kernel adds the free-face remainder per cell.
+__global__ void k_kt_exchange(Geom g, ExchangeFold ex, double scale, const float* __restrict__ Kt,
+                              float* __restrict__ Kt_ex) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)6 * g.Hx * g.Hy * g.Hz;
+    if (t >= total) return;
+    const int c = (int)(t % 6);
+    const int ky = (int)((t / 6) % g.Hy);
+    const int kz = (int)((t / ((size_t)6 * g.Hy)) % g.Hz);
+    const int kx = (int)(t / ((size_t)6 * g.Hy * g.Hz));
+    double e = 0.0;
+    if (c == 0 || c == 3 || c == 5) {
+        if (g.nx > 1) e += (2.0 * cospi(2.0 * kx / g.Lx) - 2.0) * ex.idx2;
+        if (g.ny > 1) e += (2.0 * cospi(2.0 * ky / g.Ly) - 2.0) * ex.idy2;
+        if (g.nz > 1) e += (2.0 * cospi(2.0 * kz / g.Lz) - 2.0) * ex.idz2;
+        e *= ex.pexch * scale;
+    }
+    Kt_ex[t] = (float)((double)Kt[t] + e);
+}
+
+cudaError_t tensor_fold_exchange3(const Geom& g, ExchangeFold ex, const float* Kt, float* Kt_ex, cudaStream_t s) {
+    const size_t n = (size_t)6 * g.Hx * g.Hy * g.Hz;
+    const int T = 256;
+    k_kt_exchange<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(g, ex, 1.0 / ((double)g.Lx * g.Ly * g.Lz), Kt, Kt_ex);
+    return cudaGetLastError();
+}
+
 }  // namespace mmk

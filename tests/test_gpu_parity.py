@@ -393,7 +393,7 @@ def test_thick_samples_split_pass(grid):
     cell = (4e-9, 4e-9, 4e-9)
     M = inputs.random_unit_m(grid, MS, seed=51)
     ctx = _ctx(grid, cell, Ku=1e4, alpha=0.3)
-    assert _mm().mm_plan_info(ctx)[1] == 5
+    assert _mm().mm_plan_info(ctx)[1] in (4, 5)          # 4: compile-time split + x-step kernel
     Md = _dev(M)
     Hd = torch.empty_like(Md)
     _mm().mm_demag_field(ctx, Md, Hd)
