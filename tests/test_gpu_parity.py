@@ -91,7 +91,8 @@ def test_demag_field(grid):
     assert rel_max(got, ref) < 1e-5
 
 
-@pytest.mark.parametrize("grid", [(24, 20, 4), (64, 32, 4), (32, 64, 2), (128, 16, 8), (16, 16, 1)])
+@pytest.mark.parametrize("grid", [(24, 20, 4), (64, 32, 4), (32, 64, 2), (128, 16, 8), (16, 16, 1), (16, 32, 16),
+                                  (16, 512, 8)])
 def test_effective_field(grid):
     """H_eff of Eq. (2) against the oracle: the three-pass path (24x20x4)
     and, on power-of-two films, the plane kernel with the exchange-folded
