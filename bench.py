@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -121,8 +122,14 @@ class ClockSampler:
         self.path = None
 
     def start(self):
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        # raw samples go to MM_CLOCKS_CSV when set, else to a temporary file
+        # removed after parsing; the summary is part of the JSON line
+        self.keep = bool(os.environ.get("MM_CLOCKS_CSV"))
+        if self.keep:
+            self.path = os.environ["MM_CLOCKS_CSV"]
+        else:
+            fd, self.path = tempfile.mkstemp(prefix="mm_clocks_", suffix=".csv")
+            os.close(fd)
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
@@ -145,6 +152,8 @@ class ClockSampler:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
                 rows.append(parts)
+        if not self.keep:
+            os.remove(self.path)
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
