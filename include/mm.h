@@ -150,8 +150,11 @@ int mm_get_m(mm_ctx *ctx, float *M);
  * mm_demag_field -- H_demag of M by the padded FFT convolution:
  * forward x R2C (pruned), forward y/z FFT (pruned), 3x3 real-tensor product
  * (Eq. (13)/(15)), inverse z/y (pruned), inverse x C2R keeping i < nx
- * (Eq. (10)/(16)).  M_dev, H_dev: 3*N float32 device arrays, must not
- * overlap.  Does not touch the context's own M.  Asynchronous.
+ * (Eq. (10)/(16)); on power-of-two films the z part is the exact direct sum
+ * over the layers with the (x, y) spectrum of each z offset.  M_dev, H_dev:
+ * 3*N float32 device arrays, must not overlap.  Does not touch the
+ * context's own M (it does overwrite the context's spectrum workspace, so
+ * the next mm_step re-forms it).  Asynchronous.
  */
 int mm_demag_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
 
@@ -168,9 +171,11 @@ int mm_effective_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
  * M <- Ms * (M + dt f(M)) / |M + dt f(M)|, every field term at M^n).  An
  * Euler step is three kernels (x R2C; per-kx-plane y/z FFT + tensor product
  * + inverse y/z; inverse x C2R fused with exchange, anisotropy, Zeeman, LLG,
- * Euler and renormalisation), two on power-of-two grids where the next
- * step's x R2C is fused into the update kernel; steps are replayed from
- * CUDA graphs.  n >= 0, dt > 0.
+ * Euler and renormalisation), two on power-of-two films (the next step's x
+ * R2C is fused into the update kernel and the exchange stencil into the
+ * tensor spectrum), four on thick power-of-two samples; steps are replayed
+ * from CUDA graphs of 16 steps (the remainder one step each).  n >= 0,
+ * dt > 0.
  * Asynchronous: a non-finite result is reported by mm_sync / mm_energy.
  */
 int mm_step(mm_ctx *ctx, int n, double dt);
@@ -196,7 +201,8 @@ const char *mm_last_error(const mm_ctx *ctx);
 /*
  * mm_plan_info -- the padded lengths and the decomposition chosen by
  * mm_create.  L: {Lx, Ly, Lz} (may be NULL).  Returns the number of kernel
- * launches per step (>= 3) or a negative error code.
+ * launches per Euler step (2 on power-of-two films, 4 on thick power-of-two
+ * samples, 3 or 5 otherwise) or a negative error code.
  */
 int mm_plan_info(const mm_ctx *ctx, int L[3]);
 
