@@ -454,25 +454,16 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     }
     __syncthreads();
     if constexpr (MODE == kModeStep) {
-        // ---- forward x of the new rows (first pass of the next step); the
-        // groups of a warp share the half where they can, so that the odd
-        // half's twiddle multiply does not diverge within a warp
-        constexpr int GW = G <= 32 ? 32 / G : 1;
-        int lf = line, hf = h;
-        if constexpr (GW >= 2 && NL % GW == 0) {
-            const int wq = grp / GW, s = grp % GW;
-            hf = wq & 1;
-            lf = (wq >> 1) * GW + s;
-        }
+        // ---- forward x of the new rows (first pass of the next step)
         if (fft_thread && t < Q) {
-            const float* ra = Mn + (size_t)((lf / RP) * R + 2 * (lf % RP)) * N;
+            const float* ra = Mn + (size_t)(lc * R + 2 * pr) * N;
             const float* rb = ra + N;
 #pragma unroll
             for (int q = 0; q < P; ++q) {
                 const int jx = t + Q * q;
                 v[q] = make_float2(ra[jx], rb[jx]);
             }
-            if (hf) F::odd_input_tab(v, t, tw);
+            if (h) F::odd_input_tab(v, t, tw);
             F::stepA_tab(v, t, ta, wk + grp * F::EX, false);
         }
         __syncthreads();
@@ -480,7 +471,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         __syncthreads();
         if (fft_thread && t < P) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) wk[lf * ZS + hf * HOFF + t + P * q] = w[q];   // Z[2 n + h]
+            for (int q = 0; q < Q; ++q) wk[line * ZS + h * HOFF + t + P * q] = w[q];   // Z[2 n + h]
         }
         __syncthreads();
         // split each pair into the two rows' half-spectra and store to Snext;
