@@ -439,3 +439,39 @@ def test_runge_kutta_steps_match_oracle(method, grid):
     _mm().mm_sync(ctx)
     ref_e = L.run_euler(M.astype(np.float64), 2, dt, cell, MS, A_EX, Ku, alpha, GAMMA, Hext, Kt, Lp)
     assert rel_l2(_host(out, grid), ref_e) < 1e-5
+
+
+def _random_grids(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        g = (int(rng.integers(1, 41)), int(rng.integers(1, 41)), int(rng.integers(1, 13)))
+        if g[0] * g[1] * g[2] >= 2 and g not in out:
+            out.append(g)
+    return out
+
+
+@pytest.mark.parametrize("grid", _random_grids(16, seed=2024) + [(16, 64, 12), (32, 16, 24), (64, 48, 2)])
+def test_random_grid_sizes_demag_and_step(grid):
+    """Seeded random sizes (every padded length the plan can pick, odd and
+    prime extents, thin and thick samples, plus power-of-two and mixed cases):
+    H_demag per evaluation and two Euler steps against the oracle."""
+    cell = (4e-9, 3e-9, 2e-9)
+    M = inputs.random_unit_m(grid, MS, seed=sum(grid) + 7)
+    ctx = _ctx(grid, cell, Ku=2e4, alpha=0.2)
+    _mm().mm_set_field(ctx, (1e4, -5e3, 2e3))
+    Md = _dev(M)
+    Hd = torch.empty_like(Md)
+    _mm().mm_demag_field(ctx, Md, Hd)
+    Kt, Lp = oracle_spectrum(grid, cell)
+    M64 = M.astype(np.float64)
+    Href = D.demag_fft(M64, Kt, Lp)
+    assert rel_l2(_host(Hd, grid), Href) < 1e-5
+    _mm().mm_set_m(ctx, Md)
+    _mm().mm_step(ctx, 2, 2e-14)
+    out = torch.empty_like(Md)
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    ref = L.run_euler(M64, 2, 2e-14, cell, MS, A_EX, 2e4, 0.2, GAMMA, (1e4, -5e3, 2e3), Kt, Lp)
+    assert rel_l2(_host(out, grid) - M64, ref - M64) < 1e-4
+    assert rel_l2(_host(out, grid), ref) < 1e-6
