@@ -171,11 +171,11 @@ int mm_effective_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
  * M <- Ms * (M + dt f(M)) / |M + dt f(M)|, every field term at M^n).  An
  * Euler step is three kernels (x R2C; per-kx-plane y/z FFT + tensor product
  * + inverse y/z; inverse x C2R fused with exchange, anisotropy, Zeeman, LLG,
- * Euler and renormalisation), two on power-of-two films (the next step's x
- * R2C is fused into the update kernel and the exchange stencil into the
- * tensor spectrum), four on thick power-of-two samples; steps are replayed
- * from CUDA graphs of 16 steps (the remainder one step each).  n >= 0,
- * dt > 0.
+ * Euler and renormalisation); the update kernel also forms the next step's
+ * x R2C, so a film step is two kernels (on power-of-two films the exchange
+ * stencil rides in the tensor spectrum) and a thick sample's four; steps are
+ * replayed from CUDA graphs of 16 steps (the remainder one step each).
+ * n >= 0, dt > 0.
  * Asynchronous: a non-finite result is reported by mm_sync / mm_energy.
  */
 int mm_step(mm_ctx *ctx, int n, double dt);
@@ -201,8 +201,9 @@ const char *mm_last_error(const mm_ctx *ctx);
 /*
  * mm_plan_info -- the padded lengths and the decomposition chosen by
  * mm_create.  L: {Lx, Ly, Lz} (may be NULL).  Returns the number of kernel
- * launches per Euler step (2 on power-of-two films, 4 on thick power-of-two
- * samples, 3 or 5 otherwise) or a negative error code.
+ * launches per Euler step (2 on films, 4 on thick samples whose pass 2 is
+ * split into y / z / y kernels; 3 or 5 when only the x passes are
+ * compile-time) or a negative error code.
  */
 int mm_plan_info(const mm_ctx *ctx, int L[3]);
 

@@ -25,10 +25,12 @@ __global__ void __launch_bounds__(256) k_pass1(Geom g, int R, int group, const f
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_pass3(Geom g, int R, int group, LlgCoef cf,
-                                                const float2* __restrict__ S, const float* __restrict__ M,
+                                                const float2* S, const float* __restrict__ M,
                                                 float* __restrict__ out, int* __restrict__ flag) {
     pdl_wait();
-    pass3_body<MODE>(g, R, group, cf, S, M, out, flag, blockIdx.x);
+    // kModeStepX writes the next step's x spectrum back over S
+    pass3_body<MODE>(g, R, group, cf, S, M, out, flag, blockIdx.x,
+                     MODE == kModeStepX ? const_cast<float2*>(S) : nullptr);
 }
 
 // -------------------------------------------------------------- launchers --
@@ -52,8 +54,11 @@ cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
     } else {
         e = cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem1);
         if (e != cudaSuccess) return e;
-        for (int m = 0; m < 3 && e == cudaSuccess; ++m)
-            e = cudaFuncSetAttribute(m == 0 ? k_pass3<kModeDemag> : m == 1 ? k_pass3<kModeHeff> : k_pass3<kModeStep>,
+        for (int m = 0; m < 4 && e == cudaSuccess; ++m)
+            e = cudaFuncSetAttribute(m == 0   ? k_pass3<kModeDemag>
+                                     : m == 1 ? k_pass3<kModeHeff>
+                                     : m == 2 ? k_pass3<kModeStep>
+                                              : k_pass3<kModeStepX>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem3);
         if (e != cudaSuccess) return e;
     }
@@ -111,6 +116,7 @@ cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t
 cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int mode, const float2* S,
                          const float* M, float* out, int* flag, cudaStream_t s) {
     if (l.fx) {
+        if (mode == kModeStepX) return cudaErrorInvalidValue;      // generic kernels only
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = pdl_cfg(g.nz * (g.ny / l.fx->r3), l.fx->t3, l.fx->s3, s, attr);
         return cudaLaunchKernelEx(&cfg, l.fx->p3[mode], g, c, S, M, out, flag);
@@ -121,6 +127,7 @@ cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int m
     switch (mode) {
         case kModeDemag: return cudaLaunchKernelEx(&cfg, k_pass3<kModeDemag>, g, l.r3, l.g3, c, S, M, out, flag);
         case kModeHeff: return cudaLaunchKernelEx(&cfg, k_pass3<kModeHeff>, g, l.r3, l.g3, c, S, M, out, flag);
+        case kModeStepX: return cudaLaunchKernelEx(&cfg, k_pass3<kModeStepX>, g, l.r3, l.g3, c, S, M, out, flag);
         default: return cudaLaunchKernelEx(&cfg, k_pass3<kModeStep>, g, l.r3, l.g3, c, S, M, out, flag);
     }
 }

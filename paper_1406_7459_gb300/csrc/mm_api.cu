@@ -67,6 +67,7 @@ struct mm_ctx {
     FastSplitFns fsplit;       // compile-time split pass 2 (thick power-of-two samples)
     bool has_fs = false;
     bool has_ss = false;       // thick power-of-two samples: split pass 2 + the x-step kernel
+    bool has_gx = false;       // generic x passes: the step's pass 3 also forms the next x spectrum
     float* Kt_ex = nullptr;    // tensor spectrum with the exchange stencil folded in (has_ss)
     float2* Sh = nullptr;      // plane-kernel output of the two-kernel step (layout of S)
     int method = MM_INTEGRATOR_EULER;
@@ -208,6 +209,9 @@ static int build_plan(mm_ctx* c) {
         c->has_ss = !ok && l.split && l.fs2 && s.kb[kModeStep] && g.ny % s.rb == 0 && s.sb <= smem_cap &&
                     3.0 * g.Hx * g.nz * g.Jst < (double)INT_MAX && 3.0 * g.N < (double)INT_MAX;
         if (c->has_ss) s.ka = nullptr;
+    }
+    if (!c->has_fs && !c->has_ss && !l.fx) {
+        c->has_gx = true;
     }
     return MM_OK;
 }
@@ -539,6 +543,13 @@ static int enqueue_step(mm_ctx* c, int p, double dt, cudaStream_t s) {
                               c->Mbuf[1 - p], c->flag, s));
         return MM_OK;
     }
+    if (c->has_gx) {
+        // S holds the x spectrum of M[p]: plane pass, then the update that
+        // also forms the x spectrum of M[1-p]
+        CU(launch_plane(c->g, c->l, c->S, s));
+        CU(launch_pass3(c->g, c->l, make_coef(c, dt), kModeStepX, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag, s));
+        return MM_OK;
+    }
     return run_passes(c, kModeStep, c->Mbuf[p], c->Mbuf[1 - p], dt, s);
 }
 
@@ -576,7 +587,7 @@ static int capture_step(mm_ctx* c, int kind, int p, double dt) {
 
 // Form S[cur] from M[cur] when the two-kernel step needs it.
 static int ensure_spectrum(mm_ctx* c) {
-    if (!(c->has_fs || c->has_ss) || c->spec_valid || c->method != MM_INTEGRATOR_EULER) return MM_OK;
+    if (!(c->has_fs || c->has_ss || c->has_gx) || c->spec_valid || c->method != MM_INTEGRATOR_EULER) return MM_OK;
     CU(launch_pass1(c->g, c->l, c->Mbuf[c->cur], c->S, c->stream));
     c->spec_valid = true;
     return MM_OK;
@@ -757,6 +768,7 @@ extern "C" int mm_plan_info(const mm_ctx* c, int L[3]) {
         L[1] = c->g.Ly;
         L[2] = c->g.Lz;
     }
+    if (c->has_gx) return c->l.split ? 4 : 2;
     return c->has_fs ? 2 : (c->has_ss ? 4 : (c->l.split ? 5 : 3));
 }
 

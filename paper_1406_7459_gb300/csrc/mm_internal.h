@@ -73,7 +73,9 @@ struct Launch {
     const FastSplitFns* fs2 = nullptr;  // compile-time split kernels, if the grid has them
 };
 
-enum Pass3Mode { kModeDemag = 0, kModeHeff = 1, kModeStep = 2 };
+// kModeStepX (generic kernels only): the Euler step followed by the forward
+// x R2C of the new rows into S, the first pass of the next step.
+enum Pass3Mode { kModeDemag = 0, kModeHeff = 1, kModeStep = 2, kModeStepX = 3 };
 
 // Planning helpers (mm_api.cu), shared with the batched driver.
 int plan_padded_length(int n);

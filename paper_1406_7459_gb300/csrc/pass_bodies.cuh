@@ -50,8 +50,9 @@ __device__ __forceinline__ void pass1_body(const Geom& g, int R, int group, cons
 // ---------------------------------------------------------------- pass 3 --
 template <int MODE>
 __device__ __forceinline__ void pass3_body(const Geom& g, int R, int group, const LlgCoef& cf,
-                                           const float2* __restrict__ S, const float* __restrict__ M,
-                                           float* __restrict__ out, int* __restrict__ flag, int tile) {
+                                           const float2* S, const float* __restrict__ M,
+                                           float* __restrict__ out, int* __restrict__ flag, int tile,
+                                           float2* Snext = nullptr) {
     extern __shared__ float2 sm[];
     const int lstride = padded_len(g.Lx);
     const int ntj = (g.ny + R - 1) / R;
@@ -84,7 +85,15 @@ __device__ __forceinline__ void pass3_body(const Geom& g, int R, int group, cons
         const int r = idx / g.nx;
         const int i = idx - r * g.nx;
         const int j = j0 + r;
-        if (j >= g.ny) continue;
+        if (j >= g.ny) {
+            if (MODE == kModeStepX) {
+                // a row past the sample: zero, as the x pass would read it
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    reinterpret_cast<float*>(sm + (c * half + (r >> 1)) * lstride + padi(i))[r & 1] = 0.f;
+            }
+            continue;
+        }
         float hd[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -139,6 +148,37 @@ __device__ __forceinline__ void pass3_body(const Geom& g, int R, int group, cons
         out[cell] = o0;
         out[N + cell] = o1;
         out[2 * N + cell] = o2;
+        if (MODE == kModeStepX) {
+            // the new row values replace this row's half of the pair line
+            // (each float is read above and written here by this thread only)
+            reinterpret_cast<float*>(sm + (0 * half + (r >> 1)) * lstride + padi(i))[r & 1] = o0;
+            reinterpret_cast<float*>(sm + (1 * half + (r >> 1)) * lstride + padi(i))[r & 1] = o1;
+            reinterpret_cast<float*>(sm + (2 * half + (r >> 1)) * lstride + padi(i))[r & 1] = o2;
+        }
+    }
+    if (MODE == kModeStepX) {
+        // forward x R2C of the new rows (inputs beyond nx are taken as zero),
+        // then the split into the rows' half-spectra, into Snext (which may
+        // be S itself: this tile read exactly these (kx, c, k, j) entries at
+        // its start)
+        fft_lines(sm, sm + 3 * half * lstride, lstride, 3 * half, group, g.px, g.twx, g.nx, false);
+        __syncthreads();
+        float2* Sw = Snext;
+        for (int idx = threadIdx.x; idx < 3 * g.Hx * R; idx += blockDim.x) {
+            const int r = idx % R;
+            const int t = idx / R;
+            const int kx = t % g.Hx;
+            const int c = t / g.Hx;
+            const int j = j0 + r;
+            if (j >= g.ny) continue;
+            const float2* line = sm + (c * half + (r >> 1)) * lstride;
+            const float2 zk = line[padi(kx)];
+            const float2 zm = line[padi(kx == 0 ? 0 : g.Lx - kx)];
+            float2 o;
+            if ((r & 1) == 0) o = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            else o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+            Sw[(((size_t)kx * 3 + c) * g.nz + k) * g.Jst + j] = o;
+        }
     }
 }
 
