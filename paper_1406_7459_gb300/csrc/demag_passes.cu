@@ -69,32 +69,15 @@ cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
     if (!pf) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem2);
 }
-
-// Launch configuration with programmatic serialisation: every pass kernel
-// waits on griddepcontrol before touching M, S or its output, so each may
-// start while the previous kernel on the stream drains.
-static cudaLaunchConfig_t pdl_cfg(int grid, int threads, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cfg;
-}
-
 cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s) {
     if (l.fx) {
         cudaLaunchAttribute attr[1];
-        cudaLaunchConfig_t cfg = pdl_cfg(3 * g.nz * (g.ny / l.fx->r1), l.fx->t1, l.fx->s1, s, attr);
+        cudaLaunchConfig_t cfg = launch_config(dim3(3 * g.nz * (g.ny / l.fx->r1)), l.fx->t1, l.fx->s1, s, attr);
         return cudaLaunchKernelEx(&cfg, l.fx->p1, g, M, S);
     }
     const int ntj = (g.ny + l.r1 - 1) / l.r1;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = pdl_cfg(3 * g.nz * ntj, l.t1, l.smem1, s, attr);
+    cudaLaunchConfig_t cfg = launch_config(dim3(3 * g.nz * ntj), l.t1, l.smem1, s, attr);
     return cudaLaunchKernelEx(&cfg, k_pass1, g, l.r1, l.g1, M, S);
 }
 
@@ -103,13 +86,13 @@ cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t
     if (l.split) return launch_split_plane(g, S, s);
     if (l.fp) {
         cudaLaunchAttribute attr[1];
-        cudaLaunchConfig_t cfg = pdl_cfg(g.Hx, l.fp->t2, l.fp->s2, s, attr);
+        cudaLaunchConfig_t cfg = launch_config(dim3(g.Hx), l.fp->t2, l.fp->s2, s, attr);
         return cudaLaunchKernelEx(&cfg, l.fp->pl, g, S);
     }
     PlaneFn pf = plane_fn(g.Lz);
     if (!pf) return cudaErrorInvalidValue;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = pdl_cfg(g.Hx, l.t2, l.smem2, s, attr);
+    cudaLaunchConfig_t cfg = launch_config(dim3(g.Hx), l.t2, l.smem2, s, attr);
     return cudaLaunchKernelEx(&cfg, pf, g, l.g2, S);
 }
 
@@ -118,12 +101,12 @@ cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int m
     if (l.fx) {
         if (mode == kModeStepX) return cudaErrorInvalidValue;      // generic kernels only
         cudaLaunchAttribute attr[1];
-        cudaLaunchConfig_t cfg = pdl_cfg(g.nz * (g.ny / l.fx->r3), l.fx->t3, l.fx->s3, s, attr);
+        cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / l.fx->r3)), l.fx->t3, l.fx->s3, s, attr);
         return cudaLaunchKernelEx(&cfg, l.fx->p3[mode], g, c, S, M, out, flag);
     }
     const int ntj = (g.ny + l.r3 - 1) / l.r3;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = pdl_cfg(g.nz * ntj, l.t3, l.smem3, s, attr);
+    cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * ntj), l.t3, l.smem3, s, attr);
     switch (mode) {
         case kModeDemag: return cudaLaunchKernelEx(&cfg, k_pass3<kModeDemag>, g, l.r3, l.g3, c, S, M, out, flag);
         case kModeHeff: return cudaLaunchKernelEx(&cfg, k_pass3<kModeHeff>, g, l.r3, l.g3, c, S, M, out, flag);

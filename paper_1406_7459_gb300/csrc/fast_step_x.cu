@@ -43,31 +43,17 @@ cudaError_t configure_step_kernels(const FastStepFns& f) {
     return e;
 }
 
-static cudaLaunchConfig_t step_cfg(dim3 grid, int threads, size_t smem, cudaStream_t s, bool pdl,
-                                   cudaLaunchAttribute* attr) {
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = pdl ? attr : nullptr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cfg;
-}
-
 cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, const float2* S, float2* Sh,
                           cudaStream_t s, bool pdl) {
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = step_cfg(dim3(g.Hx), f.ta, f.sa, s, pdl, attr);
+    cudaLaunchConfig_t cfg = launch_config(dim3(g.Hx), f.ta, f.sa, s, attr, pdl);
     return cudaLaunchKernelEx(&cfg, f.ka, g, Kd, S, Sh);
 }
 
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
                           const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = step_cfg(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, pdl, attr);
+    cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, attr, pdl);
     return cudaLaunchKernelEx(&cfg, f.kb[kModeStep], g, c, Sh, S, M, Mout, flag);
 }
 
@@ -76,7 +62,7 @@ cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef&
     cudaError_t e = launch_step_a(g, f, Kd, S, Sh, s, true);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = step_cfg(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, true, attr);
+    cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, attr, true);
     return cudaLaunchKernelEx(&cfg, f.kb[mode], g, c, (const float2*)Sh, (float2*)nullptr, M, out, (int*)nullptr);
 }
 

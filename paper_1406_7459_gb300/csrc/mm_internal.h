@@ -43,6 +43,24 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 #endif
 
+// Launch configuration for cudaLaunchKernelEx, with programmatic stream
+// serialisation when `pdl` (the kernel must then call pdl_wait() before it
+// touches data of earlier kernels).  attr: storage for one attribute that
+// must outlive the launch call.
+inline cudaLaunchConfig_t launch_config(dim3 grid, int threads, size_t smem, cudaStream_t s,
+                                        cudaLaunchAttribute* attr, bool pdl = true) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cfg;
+}
+
 // Row length (floats) of the 2-D spectrum Kd: Hy rounded up to 16 bytes.
 inline __host__ __device__ constexpr int kd_row(int Hy) { return (Hy + 3) & ~3; }
 

@@ -288,28 +288,15 @@ cudaError_t configure_fast_split(const FastSplitFns& f) {
     return e;
 }
 
-static cudaLaunchConfig_t split_cfg(int grid, int threads, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cfg;
-}
-
 cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, const float* Kt, float2* S, cudaStream_t s) {
     cudaLaunchAttribute attr[1];
     const int lines = g.Hx * 3 * g.nz;
     const int gy = (lines + f.ylpc - 1) / f.ylpc;
-    cudaLaunchConfig_t cy = split_cfg(gy, f.ty, f.sy, s, attr);
+    cudaLaunchConfig_t cy = launch_config(dim3(gy), f.ty, f.sy, s, attr);
     cudaError_t e = cudaLaunchKernelEx(&cy, f.yf, g, S);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cz = f.zw ? split_cfg(g.Hx * (g.Ly / f.zw), f.tz, f.sz, s, attr)
-                                 : split_cfg(1, f.tz, 0, s, attr);
+    cudaLaunchConfig_t cz = f.zw ? launch_config(dim3(g.Hx * (g.Ly / f.zw)), f.tz, f.sz, s, attr)
+                                 : launch_config(dim3(1), f.tz, 0, s, attr);
     if (!f.zw) cz.gridDim = dim3((g.Ly + f.tz - 1) / f.tz, g.Hx);
     e = cudaLaunchKernelEx(&cz, f.zc, g, Kt, S);
     if (e != cudaSuccess) return e;
@@ -324,7 +311,7 @@ cudaError_t launch_split_xstep(const Geom& g, const FastSplitFns& f2, const Fast
     // the x-step kernel reads its tile of S (all kx of R rows of a layer)
     // into shared memory before it writes the same tile back: in place
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = split_cfg(g.nz * (g.ny / fs.rb), fs.tb, fs.sb, s, attr);
+    cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / fs.rb)), fs.tb, fs.sb, s, attr);
     return cudaLaunchKernelEx(&cfg, fs.kb[mode], g, c, (const float2*)S, mode == kModeStep ? S : (float2*)nullptr,
                               M, out, mode == kModeStep ? flag : (int*)nullptr);
 }

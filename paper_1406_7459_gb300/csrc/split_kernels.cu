@@ -112,22 +112,12 @@ cudaError_t launch_split_plane(const Geom& g, float2* S, cudaStream_t s) {
     const int gy = (total + lp - 1) / lp;
     // programmatic serialisation: both kernels wait on griddepcontrol first
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cy = {};
-    cy.gridDim = dim3(gy);
-    cy.blockDim = dim3(256);
-    cy.dynamicSmemBytes = split_smem_y(g);
-    cy.stream = s;
-    cy.attrs = attr;
-    cy.numAttrs = 1;
+    cudaLaunchConfig_t cy = launch_config(dim3(gy), 256, split_smem_y(g), s, attr);
     cudaError_t e = cudaLaunchKernelEx(&cy, k_yfft, g, lp, 0, S);
     if (e != cudaSuccess) return e;
     const int W = split_chunk(g);
     const int nchunk = (g.Ly + W - 1) / W;
-    cudaLaunchConfig_t cz = cy;
-    cz.gridDim = dim3(g.Hx * nchunk);
-    cz.dynamicSmemBytes = split_smem_z(g);
+    cudaLaunchConfig_t cz = launch_config(dim3(g.Hx * nchunk), 256, split_smem_z(g), s, attr);
     e = cudaLaunchKernelEx(&cz, k_zconv, g, W, S);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cy, k_yfft, g, lp, 1, S);
