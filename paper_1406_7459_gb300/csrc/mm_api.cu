@@ -12,73 +12,24 @@
 #include <mutex>
 #include <new>
 
-#include "../../include/mm.h"
-#include "mm_internal.h"
+#include "ctx_internal.h"
 
 using namespace mmk;
 
 static thread_local char g_err[512];
 
-static int fail(int code, const char* fmt, ...) {
+namespace mmk {
+int set_error_fmt(int code, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
     return code;
 }
+}  // namespace mmk
 
-#define CU(expr)                                                                               \
-    do {                                                                                       \
-        cudaError_t _e = (expr);                                                               \
-        if (_e != cudaSuccess)                                                                 \
-            return fail(_e == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA, "%s: %s (%s:%d)", \
-                        #expr, cudaGetErrorString(_e), __FILE__, __LINE__);                    \
-    } while (0)
+#define fail mmk::set_error_fmt
 
-struct mm_ctx {
-    int grid[3];
-    double cell[3];
-    double Ms, A, Ku, alpha, gamma;
-    double Hext[3];
-    cudaStream_t stream;
-    cudaStream_t cap;          // private stream used only for graph capture
-    int device;
-    Geom g;
-    Launch l;
-    float* Kt = nullptr;
-    float* Kd = nullptr;       // 2-D spectrum per z offset, exchange folded in (two-kernel step)
-    float* Kd0 = nullptr;      // the same without exchange (two-kernel demag evaluation)
-    float2* S = nullptr;
-    float* Mbuf[2] = {nullptr, nullptr};
-    int cur = 0;
-    float* H = nullptr;
-    int* flag = nullptr;
-    double* partials = nullptr;
-    double* Edev = nullptr;
-    float2* tw = nullptr;      // twiddles of x, y, z back to back
-    // step graphs [kind][parity]: kind 0 one step, kind 1 kGraphSteps steps
-    cudaGraphExec_t step_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    double step_dt[2][2] = {{0, 0}, {0, 0}};
-    unsigned long long step_ver[2][2] = {{0, 0}, {0, 0}};
-    unsigned long long ver = 1;   // bumped when H_ext changes
-    bool use_graphs = true;
-    FastFns fast;              // compile-time kernels (when the grid has them)
-    FastStepFns fs;            // two-kernel step (power-of-two grids)
-    FastSplitFns fsplit;       // compile-time split pass 2 (thick power-of-two samples)
-    bool has_fs = false;
-    bool has_ss = false;       // thick power-of-two samples: split pass 2 + the x-step kernel
-    bool has_gx = false;       // generic x passes: the step's pass 3 also forms the next x spectrum
-    float* Kt_ex = nullptr;    // tensor spectrum with the exchange stencil folded in (has_ss)
-    float2* Sh = nullptr;      // plane-kernel output of the two-kernel step (layout of S)
-    int method = MM_INTEGRATOR_EULER;
-    float* Mst = nullptr;      // Runge-Kutta stage state
-    float* acc = nullptr;      // Runge-Kutta weighted slope sum
-    float* sur = nullptr;      // surrogate stepper: M_ref, H_ref, x, y, H_d (5 x 3N)
-    double* sur_r = nullptr;   // residual sums
-    bool spec_valid = false;   // S holds the x half-spectrum of M[cur] (two-kernel step)
-    float* dpk[7] = {};        // Dormand-Prince stage slopes (adaptive runs), 3*N each
-    unsigned* dperr = nullptr; // error estimate of the last trial step (float bits)
-};
 
 // ------------------------------------------------------------------ plan --
 static bool smooth235(int n) {
@@ -234,7 +185,7 @@ namespace mmk {
 void plan_twiddles(int L, float2* out) { host_twiddles(L, out); }
 }  // namespace mmk
 
-static LlgCoef make_coef(const mm_ctx* c, double dt) {
+LlgCoef mmk::make_coef(const mm_ctx* c, double dt) {
     LlgCoef f;
     const double Ms2 = c->Ms * c->Ms;
     const double den = 1.0 + c->alpha * c->alpha;
@@ -471,7 +422,7 @@ extern "C" int mm_get_m(mm_ctx* c, float* M) {
 
 // The three-pass evaluation on the spectrum workspace S (which also holds
 // the two-kernel step's spectrum, so it invalidates a pending one).
-static int run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt, cudaStream_t s) {
+int mmk::run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt, cudaStream_t s) {
     const LlgCoef cf = make_coef(c, dt);
     c->spec_valid = false;
     CU(launch_pass1(c->g, c->l, M, c->S, s));
@@ -618,116 +569,6 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
             ++s;
         }
     }
-    return MM_OK;
-}
-
-// ------------------------------------------------ adaptive Dormand-Prince --
-// Dormand-Prince RK5(4) (Dormand and Prince, J. Comput. Appl. Math. 6 (1980)
-// 19-26): stage rows a (row s forms stage s + 1), fifth-order weights b and
-// e = b - b_hat, b_hat the embedded fourth-order weights.
-static const double kDpA[6][6] = {
-    {0.0},
-    {1.0 / 5.0},
-    {3.0 / 40.0, 9.0 / 40.0},
-    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0},
-    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0},
-    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0}};
-static const double kDpB[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0};
-static const double kDpE[7] = {71.0 / 57600.0,      0.0,          -71.0 / 16695.0, 71.0 / 1920.0,
-                               -17253.0 / 339200.0, 22.0 / 525.0, -1.0 / 40.0};
-// Controller: accept when err <= tol; next step h * clamp(0.9 (tol/err)^(1/5),
-// 0.2, 5), no growth right after a rejection.
-static double dp_factor(double err, double tol, bool after_reject) {
-    double fac = err <= 0.0 ? 5.0 : 0.9 * std::pow(tol / err, 0.2);
-    fac = std::min(5.0, std::max(0.2, fac));
-    return after_reject ? std::min(fac, 1.0) : fac;
-}
-
-static DpWeights dp_row(const double* w, int n) {
-    DpWeights r{};
-    for (int j = 0; j < n; ++j) r.w[j] = (float)w[j];
-    return r;
-}
-
-extern "C" int mm_run_adaptive(mm_ctx* c, double t_span, double* dt_io, double tol, int max_steps,
-                               double stats[4]) {
-    if (!c || !dt_io) return fail(MM_EINVAL, "null argument");
-    if (!(t_span >= 0.0) || !std::isfinite(t_span)) return fail(MM_EINVAL, "t_span must be finite and >= 0");
-    if (!(*dt_io > 0.0) || !std::isfinite(*dt_io)) return fail(MM_EINVAL, "dt must be > 0");
-    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(MM_EINVAL, "tol must be > 0");
-    if (max_steps < 1) return fail(MM_EINVAL, "max_steps must be >= 1");
-    const size_t n3 = 3 * (size_t)c->g.N;
-    if (!c->Mst) CU(cudaMalloc(&c->Mst, sizeof(float) * n3));
-    for (int q = 0; q < 7; ++q)
-        if (!c->dpk[q]) CU(cudaMalloc(&c->dpk[q], sizeof(float) * n3));
-    if (!c->dperr) CU(cudaMalloc(&c->dperr, sizeof(unsigned)));
-    cudaStream_t s = c->stream;
-    DpPtrs kp;
-    for (int q = 0; q < 7; ++q) kp.k[q] = c->dpk[q];
-    const DpWeights we = dp_row(kDpE, 7);
-    double t = 0.0, dt = *dt_io;
-    long long acc = 0, rej = 0, nev = 0;
-    bool after_reject = false, k1_valid = false;
-    int rc = MM_OK;
-    c->spec_valid = false;
-    while (t_span - t > 1e-12 * t_span && acc + rej < max_steps) {
-        const int p = c->cur;
-        const double h = std::min(dt, t_span - t);
-        const LlgCoef cf = make_coef(c, h);
-        const float* M = c->Mbuf[p];
-        float* cand = c->Mbuf[1 - p];
-        // stage 2 state (and k1 = f(M) on the first step; later k1 is the
-        // previous step's seventh stage)
-        if (!k1_valid) {
-            rc = run_passes(c, kModeHeff, M, c->H, 0.0, s);
-            if (rc != MM_OK) return rc;
-            CU(launch_dp_stage(c->g.N, cf, kp, 1, dp_row(kDpA[1], 1), 0, M, c->H, M, c->Mst, nullptr, s));
-            nev += 1;
-            k1_valid = true;
-        } else {
-            CU(launch_dp_combine(c->g.N, kp, dp_row(kDpA[1], 1), 1, (float)h, M, c->Mst, s));
-        }
-        for (int st = 2; st <= 6; ++st) {
-            rc = run_passes(c, kModeHeff, c->Mst, c->H, 0.0, s);
-            if (rc != MM_OK) return rc;
-            const bool last = st == 6;
-            const DpWeights w = last ? dp_row(kDpB, 6) : dp_row(kDpA[st], st);
-            CU(launch_dp_stage(c->g.N, cf, kp, st, w, last ? 1 : 0, c->Mst, c->H, M, last ? cand : c->Mst, nullptr,
-                               s));
-        }
-        rc = run_passes(c, kModeHeff, cand, c->H, 0.0, s);
-        if (rc != MM_OK) return rc;
-        CU(cudaMemsetAsync(c->dperr, 0, sizeof(unsigned), s));
-        CU(launch_dp_error(c->g.N, cf, kp, we, cand, c->H, kp.k[6], c->dperr, s));
-        unsigned bits = 0;
-        CU(cudaMemcpyAsync(&bits, c->dperr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-        nev += 6;
-        float errf;
-        std::memcpy(&errf, &bits, sizeof(float));
-        const double err = (double)errf;
-        if (err <= tol) {
-            t += h;
-            c->cur = 1 - p;
-            std::swap(kp.k[0], kp.k[6]);
-            ++acc;
-            dt = h * dp_factor(err, tol, after_reject);
-            after_reject = false;
-        } else {
-            ++rej;
-            dt = h * dp_factor(std::isfinite(err) ? err : 1e300, tol, true);
-            after_reject = true;
-        }
-    }
-    for (int q = 0; q < 7; ++q) c->dpk[q] = kp.k[q];
-    *dt_io = dt;
-    if (stats) {
-        stats[0] = (double)acc;
-        stats[1] = (double)rej;
-        stats[2] = (double)nev;
-        stats[3] = t;
-    }
-    if (t_span - t > 1e-12 * t_span) return fail(MM_ELIMIT, "max_steps reached before t_span was covered");
     return MM_OK;
 }
 
@@ -920,61 +761,3 @@ extern "C" int mm_demag_field_noalloc(const int grid[3], const float* Kt_dev, co
     return MM_OK;
 }
 
-// ------------------------------------------------- surrogate-assisted step --
-extern "C" int mm_step_surrogate(mm_ctx* c, mm_fno* f, int n, double dt, int refresh, double tol, double stats[4]) {
-    if (!c || !f) return fail(MM_EINVAL, "null context or surrogate");
-    if (n < 0 || refresh < 1 || !(dt > 0.0) || !(tol > 0.0)) return fail(MM_EINVAL, "bad n, refresh, dt or tol");
-    if (!fno_matches(f, c->g.nx, c->g.ny, c->g.nz))
-        return fail(MM_EINVAL, "surrogate grid does not match the film (nz must be 1)");
-    const size_t N3 = 3 * (size_t)c->g.N;
-    if (!c->sur) {
-        CU(cudaMalloc(&c->sur, sizeof(float) * 5 * N3));
-        CU(cudaMalloc(&c->sur_r, 2 * sizeof(double)));
-    }
-    float *Mref = c->sur, *Href = c->sur + N3, *x = c->sur + 2 * N3, *y = c->sur + 3 * N3, *Hd = c->sur + 4 * N3;
-    const LlgCoef cf = make_coef(c, dt);
-    const float Ms = (float)c->Ms;
-    double n_sur = 0, n_exact = 0, max_res = 0;
-    bool fallback = false, have_ref = false;
-    for (int s = 0; s < n; ++s) {
-        const int p = c->cur;
-        if (s % refresh == 0 || fallback) {
-            int rc = run_passes(c, kModeDemag, c->Mbuf[p], Hd, 0.0, c->stream);
-            if (rc != MM_OK) return rc;
-            if (have_ref && !fallback) {
-                // surrogate's prediction at this state against the exact field
-                CU(sur_scaled_diff(c->Mbuf[p], Mref, 1.f / Ms, (long long)N3, x, c->stream));
-                rc = fno_apply(f, x, y, c->stream);
-                if (rc != MM_OK) return rc;
-                CU(sur_axpy(Href, y, Ms, (long long)N3, x, c->stream));
-                CU(sur_resid(x, Hd, (long long)N3, c->sur_r, c->stream));
-                double r[2];
-                CU(cudaMemcpyAsync(r, c->sur_r, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
-                CU(cudaStreamSynchronize(c->stream));
-                const double res = r[1] > 0 ? std::sqrt(r[0] / r[1]) : 0.0;
-                if (res > max_res) max_res = res;
-                if (res > tol) fallback = true;
-            }
-            CU(cudaMemcpyAsync(Mref, c->Mbuf[p], sizeof(float) * N3, cudaMemcpyDeviceToDevice, c->stream));
-            CU(cudaMemcpyAsync(Href, Hd, sizeof(float) * N3, cudaMemcpyDeviceToDevice, c->stream));
-            have_ref = true;
-            n_exact += 1;
-        } else {
-            CU(sur_scaled_diff(c->Mbuf[p], Mref, 1.f / Ms, (long long)N3, x, c->stream));
-            int rc = fno_apply(f, x, y, c->stream);
-            if (rc != MM_OK) return rc;
-            CU(sur_axpy(Href, y, Ms, (long long)N3, Hd, c->stream));
-            n_sur += 1;
-        }
-        CU(sur_llg(c->g, cf, c->Mbuf[p], Hd, c->Mbuf[1 - p], c->flag, c->stream));
-        c->cur = 1 - p;
-    }
-    c->spec_valid = false;
-    if (stats) {
-        stats[0] = n_sur;
-        stats[1] = n_exact;
-        stats[2] = max_res;
-        stats[3] = fallback ? 1.0 : 0.0;
-    }
-    return MM_OK;
-}
