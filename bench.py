@@ -264,7 +264,8 @@ def run_gpu(args, rank, ws):
     dt = w["dt"]
     K, W = args.steps, args.warmup
 
-    sampler = ClockSampler(local)
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    sampler = ClockSampler(vis[local] if local < len(vis) else local)     # nvidia-smi numbering
     sampler.start()
     mm.mm_step(ctx, max(W, 3), dt)                   # warm-up (graph capture)
     torch.cuda.synchronize()
