@@ -475,3 +475,43 @@ def test_random_grid_sizes_demag_and_step(grid):
     ref = L.run_euler(M64, 2, 2e-14, cell, MS, A_EX, 2e4, 0.2, GAMMA, (1e4, -5e3, 2e3), Kt, Lp)
     assert rel_l2(_host(out, grid) - M64, ref - M64) < 1e-4
     assert rel_l2(_host(out, grid), ref) < 1e-6
+
+
+@pytest.mark.parametrize("grid", [(2048, 2, 1), (3, 2048, 1), (2, 3, 2048), (1025, 3, 2)])
+def test_longest_padded_axes(grid):
+    """The largest padded length the plan admits (4096) on each axis, and a
+    smooth length above 2048 (1025 -> 2160): demag and one step against the
+    oracle."""
+    cell = (3e-9, 3e-9, 3e-9)
+    M = inputs.random_unit_m(grid, MS, seed=77)
+    ctx = _ctx(grid, cell, Ku=1e4, alpha=0.3)
+    Md = _dev(M)
+    Hd = torch.empty_like(Md)
+    _mm().mm_demag_field(ctx, Md, Hd)
+    Kt, Lp = oracle_spectrum(grid, cell)
+    M64 = M.astype(np.float64)
+    assert rel_l2(_host(Hd, grid), D.demag_fft(M64, Kt, Lp)) < 1e-5
+    _mm().mm_set_m(ctx, Md)
+    _mm().mm_step(ctx, 1, 2e-14)
+    out = torch.empty_like(Md)
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    ref = L.run_euler(M64, 1, 2e-14, cell, MS, A_EX, 1e4, 0.3, GAMMA, (0, 0, 0), Kt, Lp)
+    assert rel_l2(_host(out, grid) - M64, ref - M64) < 1e-4
+
+
+def test_zero_and_negative_step_counts():
+    """n = 0 leaves the state untouched bit for bit; n < 0 is rejected (bad
+    create arguments are covered without a GPU in test_abi)."""
+    grid, cell = (4, 4, 4), (3e-9, 3e-9, 3e-9)
+    M = inputs.random_unit_m(grid, MS, seed=78)
+    ctx = _ctx(grid, cell)
+    _mm().mm_set_m(ctx, _dev(M))
+    _mm().mm_step(ctx, 0, 1e-13)
+    out = torch.empty(3 * ctx.N, device="cuda")
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    assert np.array_equal(out.cpu().numpy(), np.ascontiguousarray(M, np.float32).reshape(-1))
+    with pytest.raises(_mm().MMError) as e:
+        _mm().mm_step(ctx, -1, 1e-13)
+    assert e.value.code == _mm().MM_EINVAL
