@@ -7,10 +7,11 @@
 //                    nonzero inputs as the two unpadded halves of the padded
 //                    length 2 ny (fast_fft.cuh); X[2m + h] is stored at
 //                    position h*NY + m of the line, in place.
-//   k_zconv_fast<NZ> per kx and W consecutive y positions: forward z of the
-//                    3W z-lines (nz nonzero inputs), the member-wise product
-//                    with the real symmetric tensor spectrum (Eq. (15)),
-//                    inverse z keeping k < nz (Eq. (16)).
+//   k_zconv_fast<NZ> per kx and W consecutive y positions (nz >= 16):
+//                    forward z of the 3W z-lines (nz nonzero inputs), the
+//                    member-wise product with the real symmetric tensor
+//                    spectrum (Eq. (15)), inverse z keeping k < nz (Eq. (16));
+//   k_zcol_fast<NZ>  the same for nz <= 8, one y position per thread.
 //   k_yinv_fast<NY>  per batch of lines: inverse y keeping j < ny, in place.
 //
 // All three wait on griddepcontrol before touching the spectrum, so they are
@@ -104,108 +105,139 @@ __global__ void __launch_bounds__(YLayout<NY>::THREADS) k_yinv_fast(Geom g, floa
     }
 }
 
+// z convolution for nz >= 16.  A CTA takes W consecutive y positions of one
+// kx plane and keeps their 3 nz-point z lines in shared memory as [c][z][w]
+// (w fastest): every warp reads and writes whole W-wide rows, so no access
+// has a bank conflict, and the rows of S are staged with 16-byte copies.
+// Each half h of the padded z spectrum (kz = 2m + h) is one unpadded FFT of
+// length nz = P Q in the index split of Fft2, done in place:
+//   strided items (c, t, w), t < Q: positions t + Q p, DFT_P, twiddle W^{ta};
+//   block items (a, w), a < P, all three components: positions a Q + b,
+//     DFT_Q gives X[a + P b] (b < Q); the product with the tensor spectrum
+//     (Eq. (15)) for the Q wavenumbers kz = 2 (a + P b) + h; then the first
+//     step of the inverse on the conjugated product: DFT_Q over b, twiddle
+//     W^{s a}, stored at a Q + s;
+//   strided items (c, s, w): positions s + Q a, DFT_P and conjugation give
+//     the inverse transform at z = s + Q r, in natural order.
+// Half 0 works out of the input buffer xb into wb and leaves its inverse in
+// wb; half 1 works in xb in place and adds W_{2nz}^{-z} times its inverse to
+// wb's (the pruned inverse of Sec. 2, step (5)) on the way out to S.
 template <int NZ> struct ZLayout {
     using F = Fft2<NZ>;
-    static constexpr int W = cmax_i(64 / F::G, 1);            // y positions per CTA (384 threads)
-    static constexpr int THREADS = 6 * W * F::G;
-    static constexpr int ZP = 2 * NZ + 1;                        // z-line stride in shared memory
-    static constexpr int MINB = NZ >= 128 ? 3 : 1;               // CTAs per SM the registers must allow
-    static constexpr size_t BYTES = sizeof(float2) * (2 * NZ + 3 * W * ZP + 6 * W * F::EX);
+    static constexpr int W = (NZ == 16 || NZ == 32) ? 32 : 16;   // y positions per CTA
+    static constexpr int THREADS = F::P * W;                      // one block item per thread
+    static constexpr int MINB = 512 / THREADS;                    // CTAs per SM the registers must allow
+    static constexpr int LINE = NZ * W;                           // one component's lines (complex)
+    static constexpr size_t BYTES = sizeof(float2) * (2 * NZ + 6 * LINE);
 };
 
 template <int NZ>
 __global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zconv_fast(Geom g, const float* __restrict__ Kt, float2* __restrict__ S) {
     using Lay = ZLayout<NZ>;
     using F = Fft2<NZ>;
-    constexpr int P = F::P, Q = F::Q, G = F::G, T = Lay::THREADS, W = Lay::W, ZP = Lay::ZP;
-    extern __shared__ float2 sm[];
-    float2* tw = sm;                          // W_{2NZ}^k
-    float2* zs = tw + 2 * NZ;                 // [c*W + w][z], z < 2 NZ
-    float2* ex = zs + 3 * W * ZP;
+    constexpr int P = F::P, Q = F::Q, T = Lay::THREADS, W = Lay::W, LINE = Lay::LINE;
+    constexpr int NS = 3 * Q * W;             // strided items
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;                          // W_{2NZ}^k, k < 2 NZ
+    float2* xb = tw + 2 * NZ;                 // [c][z][w]
+    float2* wb = xb + 3 * LINE;
     const int nchunk = g.Ly / W;
     const int kx = blockIdx.x / nchunk;
-    const int p0 = (blockIdx.x % nchunk) * W;
-    const int NYh = g.Ly / 2;
-#pragma unroll
+    const int p0 = (blockIdx.x - kx * nchunk) * W;
     for (int i = threadIdx.x; i < 2 * NZ; i += T) tw[i] = __ldg(g.twz + i);
     pdl_wait();
-    const float2* base = S + (size_t)kx * 3 * NZ * g.Jst + p0;
+    float2* plane = S + (size_t)kx * 3 * NZ * g.Jst + p0;
 #pragma unroll
-    for (int idx = threadIdx.x; idx < 3 * NZ * W; idx += T) {
-        const int w = idx % W, ck = idx / W;          // ck = c*NZ + k
-        const int c = ck / NZ, k = ck % NZ;
-        zs[(c * W + w) * ZP + k] = base[(size_t)ck * g.Jst + w];
+    for (int i = threadIdx.x; i < 3 * NZ * (W / 2); i += T) {
+        const int ck = i / (W / 2), j = i - ck * (W / 2);
+        __pipeline_memcpy_async(xb + ck * W + 2 * j, plane + (size_t)ck * g.Jst + 2 * j, 2 * sizeof(float2));
     }
+    __pipeline_commit();
+    // this thread's y position (the same in every item: T is a multiple of W)
+    const int w = threadIdx.x % W, a = threadIdx.x / W;
+    const int NYh = g.Ly / 2;
+    const int py = p0 + w;
+    const int ky = 2 * (py % NYh) + py / NYh;             // the forward y kernel's order
+    int kyp = ky;
+    float sy = 1.f;
+    if (2 * ky > g.Ly) { kyp = g.Ly - ky; sy = -1.f; }
+    const float* Kp = Kt + ((size_t)kx * g.Hz * g.Hy + kyp) * 6;
+    __pipeline_wait_prior(0);
     __syncthreads();
-    const int grp = threadIdx.x / G, t = threadIdx.x % G;
-    const int zl = grp >> 1, h = grp & 1;              // z-line zl = c*W + w
-    float2* zln = zs + zl * ZP;
-    // forward z, pruned input: Z[2 m + h] at position h*NZ + m
-    if (t < Q) {
-        float2 v[P];
 #pragma unroll
-        for (int q = 0; q < P; ++q) v[q] = zln[t + Q * q];
-        if (h) F::odd_input(v, t, tw);
-        F::stepA(v, t, tw, ex + grp * F::EX, false);
-    }
-    __syncthreads();
-    if (t < P) {
-        float2 w[Q];
-        F::stepB(w, t, ex + grp * F::EX, false);
+    for (int h = 0; h < 2; ++h) {
+        float2* buf = h ? xb : wb;
+        // forward, strided items: xb -> buf
 #pragma unroll
-        for (int q = 0; q < Q; ++q) zln[h * NZ + t + P * q] = w[q];
-    }
-    __syncthreads();
-    // tensor product per (y position, kz); the y position p holds
-    // ky = 2 (p mod ny) + p / ny (the forward y kernel's order)
-    const float* Kp = Kt + (size_t)kx * g.Hz * g.Hy * 6;
+        for (int i = threadIdx.x; i < NS; i += T) {
+            const int t = (i / W) % Q, c = i / (W * Q);
+            float2 v[P];
 #pragma unroll
-    for (int idx = threadIdx.x; idx < W * 2 * NZ; idx += T) {
-        const int w = idx % W, zp = idx / W;
-        const int kz = 2 * (zp % NZ) + zp / NZ;
-        const int p = p0 + w;
-        const int ky = 2 * (p % NYh) + p / NYh;
-        int kyp = ky, kzp = kz;
-        float sy = 1.f, sz = 1.f;
-        if (2 * ky > g.Ly) { kyp = g.Ly - ky; sy = -1.f; }
-        if (2 * kz > g.Lz) { kzp = g.Lz - kz; sz = -1.f; }
-        const float* kk = Kp + ((size_t)kzp * g.Hy + kyp) * 6;
-        const float kxx = __ldg(kk + 0), kxy = sy * __ldg(kk + 1), kxz = sz * __ldg(kk + 2);
-        const float kyy = __ldg(kk + 3), kyz = sy * sz * __ldg(kk + 4), kzz = __ldg(kk + 5);
-        const float2 mx = zs[(0 * W + w) * ZP + zp];
-        const float2 my = zs[(1 * W + w) * ZP + zp];
-        const float2 mz = zs[(2 * W + w) * ZP + zp];
-        zs[(0 * W + w) * ZP + zp] = make_float2(kxx * mx.x + kxy * my.x + kxz * mz.x, kxx * mx.y + kxy * my.y + kxz * mz.y);
-        zs[(1 * W + w) * ZP + zp] = make_float2(kxy * mx.x + kyy * my.x + kyz * mz.x, kxy * mx.y + kyy * my.y + kyz * mz.y);
-        zs[(2 * W + w) * ZP + zp] = make_float2(kxz * mx.x + kyz * my.x + kzz * mz.x, kxz * mx.y + kyz * my.y + kzz * mz.y);
-    }
-    __syncthreads();
-    // inverse z, pruned output: x[k] = IFFT(even)[k] + W^{-k} IFFT(odd)[k]
-    float2 w[Q];
-    if (t < Q) {
-        float2 v[P];
+            for (int p = 0; p < P; ++p) v[p] = xb[(c * NZ + t + Q * p) * W + w];
+            if (h) F::odd_input(v, t, tw);
+            F::stepA_reg(v, t, tw, false);
 #pragma unroll
-        for (int q = 0; q < P; ++q) v[q] = zln[h * NZ + t + Q * q];
-        F::stepA(v, t, tw, ex + grp * F::EX, true);
-    }
-    __syncthreads();
-    if (t < P) {
-        F::stepB(w, t, ex + grp * F::EX, true);
-        if (h) F::odd_output(w, t, tw);
-    }
-    __syncthreads();                          // zs is rewritten below
-    if (t < P) {
+            for (int p = 0; p < P; ++p) buf[(c * NZ + t + Q * p) * W + w] = v[p];
+        }
+        __syncthreads();
+        // block items: DFT_Q, tensor product, first inverse step
+        {
+            float2 u[3][Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) zln[h * NZ + t + P * q] = w[q];
-    }
-    __syncthreads();
-    float2* out = S + (size_t)kx * 3 * NZ * g.Jst + p0;
+            for (int c = 0; c < 3; ++c) {
 #pragma unroll
-    for (int idx = threadIdx.x; idx < 3 * NZ * W; idx += T) {
-        const int w2 = idx % W, ck = idx / W;
-        const int c = ck / NZ, k = ck % NZ;
-        const float2* l = zs + (c * W + w2) * ZP;
-        out[(size_t)ck * g.Jst + w2] = cadd(l[k], l[NZ + k]);
+                for (int b = 0; b < Q; ++b) u[c][b] = buf[(c * NZ + a * Q + b) * W + w];
+                dftp<Q>(u[c]);
+            }
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+                const int kz = 2 * (a + P * b) + h;
+                int kzp = kz;
+                float sz = 1.f;
+                if (kz > NZ) { kzp = 2 * NZ - kz; sz = -1.f; }
+                const float2* kk = reinterpret_cast<const float2*>(Kp + (size_t)kzp * g.Hy * 6);
+                const float2 k01 = __ldg(kk), k23 = __ldg(kk + 1), k45 = __ldg(kk + 2);
+                const float kxx = k01.x, kxy = sy * k01.y, kxz = sz * k23.x;
+                const float kyy = k23.y, kyz = sy * sz * k45.x, kzz = k45.y;
+                const float2 mx = u[0][b], my = u[1][b], mz = u[2][b];
+                // conjugated product: the inverse runs as conj(DFT(conj(.)))
+                u[0][b] = make_float2(kxx * mx.x + kxy * my.x + kxz * mz.x, -(kxx * mx.y + kxy * my.y + kxz * mz.y));
+                u[1][b] = make_float2(kxy * mx.x + kyy * my.x + kyz * mz.x, -(kxy * mx.y + kyy * my.y + kyz * mz.y));
+                u[2][b] = make_float2(kxz * mx.x + kyz * my.x + kzz * mz.x, -(kxz * mx.y + kyz * my.y + kzz * mz.y));
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dftp<Q>(u[c]);
+#pragma unroll
+                for (int s2 = 0; s2 < Q; ++s2) {
+                    const float2 v = s2 ? cmul(u[c][s2], tw[2 * s2 * a]) : u[c][s2];
+                    buf[(c * NZ + a * Q + s2) * W + w] = v;
+                }
+            }
+        }
+        __syncthreads();
+        // inverse, strided items: natural order, conjugated back
+#pragma unroll
+        for (int i = threadIdx.x; i < NS; i += T) {
+            const int s2 = (i / W) % Q, c = i / (W * Q);
+            float2 v[P];
+#pragma unroll
+            for (int r = 0; r < P; ++r) v[r] = buf[(c * NZ + s2 + Q * r) * W + w];
+            dftp<P>(v);
+            if (h == 0) {
+#pragma unroll
+                for (int r = 0; r < P; ++r) wb[(c * NZ + s2 + Q * r) * W + w] = cconj(v[r]);
+            } else {
+                // x[z] = y0[z] + W_{2NZ}^{-z} y1[z],  z = s2 + Q r
+                F::odd_input(v, s2, tw);
+#pragma unroll
+                for (int r = 0; r < P; ++r) {
+                    const int z = s2 + Q * r;
+                    plane[(size_t)(c * NZ + z) * g.Jst + w] = cadd(wb[(c * NZ + z) * W + w], cconj(v[r]));
+                }
+            }
+        }
+        // half 1 reads only xb (untouched by half 0) before its next barrier
     }
 }
 
