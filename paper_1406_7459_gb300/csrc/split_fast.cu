@@ -125,8 +125,12 @@ __global__ void __launch_bounds__(YLayout<NY>::THREADS) k_yinv_fast(Geom g, floa
 template <int NZ> struct ZLayout {
     using F = Fft2<NZ>;
     static constexpr int W = (NZ == 16 || NZ == 32) ? 32 : 16;   // y positions per CTA
-    static constexpr int THREADS = F::P * W;                      // one block item per thread
-    static constexpr int MINB = 512 / THREADS;                    // CTAs per SM the registers must allow
+    static constexpr int NB = F::P * W;                           // block items
+    static constexpr int NS = 3 * F::Q * W;                       // strided items
+    // one block item per thread where the strided items split evenly over
+    // them (P = Q), else one strided item per thread (P = 2Q)
+    static constexpr int THREADS = NS % NB == 0 ? NB : NS;
+    static constexpr int MINB = NS % NB == 0 ? 512 / THREADS : 2;  // CTAs per SM the registers must allow
     static constexpr int LINE = NZ * W;                           // one component's lines (complex)
     static constexpr size_t BYTES = sizeof(float2) * (2 * NZ + 6 * LINE);
 };
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zco
     using Lay = ZLayout<NZ>;
     using F = Fft2<NZ>;
     constexpr int P = F::P, Q = F::Q, T = Lay::THREADS, W = Lay::W, LINE = Lay::LINE;
-    constexpr int NS = 3 * Q * W;             // strided items
+    constexpr int NS = Lay::NS;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm;                          // W_{2NZ}^k, k < 2 NZ
     float2* xb = tw + 2 * NZ;                 // [c][z][w]
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(ZLayout<NZ>::THREADS, ZLayout<NZ>::MINB) k_zco
         }
         __syncthreads();
         // block items: DFT_Q, tensor product, first inverse step
-        {
+        if (Lay::NB == T || threadIdx.x < Lay::NB) {
             float2 u[3][Q];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
