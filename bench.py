@@ -416,7 +416,10 @@ def run_cube(args, rank, ws):
     table = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_table1.json")))
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     points = []
-    for n in inputs.CUBE_SIZES:
+    sizes = inputs.CUBE_SIZES if not args.cube_n else [int(v) for v in args.cube_n.split(",")]
+    for n in sizes:
+        if n not in inputs.CUBE_SIZES:
+            raise SystemExit("--cube-n: %d is not one of %s" % (n, inputs.CUBE_SIZES))
         grid = (n, n, n)
         ctx = mm.mm_create(grid, w["cell"], w["Ms"], w["A"], w["Ku"], w["alpha"], w["gamma"])
         mm.mm_set_m(ctx, torch.from_numpy(inputs.random_unit_m(grid, w["Ms"], w["seed"]).reshape(-1)).cuda())
@@ -635,6 +638,8 @@ def main():
     ap.add_argument("--workload", default="film", choices=["film", "cube", "batch", "surrogate"],
                     help="film: the 256x256x4 benchmark line; cube: the N^3 per-step curve; "
                          "batch: 512 uneven samples batched vs one at a time; surrogate: the FNO")
+    ap.add_argument("--cube-n", default="",
+                    help="cube workload: comma-separated subset of the sizes (default all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=None,
