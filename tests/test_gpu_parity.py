@@ -241,6 +241,46 @@ def test_direct_sum_samples_at_256x256x4():
         assert np.max(np.abs(got[:, k, j, i] - ref[s])) < 1e-5 * scale
 
 
+def test_cube_128_sampled_cells_in_the_benchmarked_plan():
+    """The N = 128 point of the cube curve at full size, in the plan that
+    `bench.py --workload cube` times (split y / z / y kernels + x-step
+    kernel, single-step graph): H_demag at sampled cells by the direct sum
+    of Eq. (12), and one Euler step of Eq. (6) at those cells from the
+    oracle's exchange, anisotropy and Zeeman terms and that H_demag."""
+    w = inputs.CUBE
+    grid, cell = (128, 128, 128), w["cell"]
+    Ms, A, Ku, alpha, gamma, dt = w["Ms"], w["A"], w["Ku"], w["alpha"], w["gamma"], w["dt"]
+    M = inputs.random_unit_m(grid, Ms, w["seed"])
+    ctx = _ctx(grid, cell, Ms=Ms, A=A, Ku=Ku, alpha=alpha, gamma=gamma)
+    assert _mm().mm_plan_info(ctx)[1] == 4
+    Md = _dev(M)
+    Hd = torch.empty_like(Md)
+    _mm().mm_demag_field(ctx, Md, Hd)
+    got = _host(Hd, grid)
+    cells = [(0, 0, 0), (127, 127, 127), (64, 31, 97)]
+    M64 = M.astype(np.float64)
+    Href = D.demag_at_cells(M64, cell, cells)
+    scale = np.max(np.abs(Href))
+    for s, (i, j, k) in enumerate(cells):
+        assert np.max(np.abs(got[:, k, j, i] - Href[s])) < 1e-5 * scale
+    _mm().mm_set_m(ctx, Md)
+    _mm().mm_set_field(ctx, w["H_ext"])
+    _mm().mm_step(ctx, 1, dt)
+    out = torch.empty_like(Md)
+    _mm().mm_get_m(ctx, out)
+    _mm().mm_sync(ctx)
+    M1 = _host(out, grid)
+    Hloc = L.h_exchange(M64, cell, Ms, A) + L.h_anisotropy(M64, Ms, Ku)
+    for s, (i, j, k) in enumerate(cells):
+        m = M64[:, k, j, i].reshape(3, 1, 1, 1)
+        H = Hloc[:, k, j, i].reshape(3, 1, 1, 1) + Href[s].reshape(3, 1, 1, 1) + \
+            np.asarray(w["H_ext"], np.float64).reshape(3, 1, 1, 1)
+        n = m + dt * L.llg_rhs(m, H, Ms, alpha, gamma)
+        n = (n * (Ms / np.sqrt(np.sum(n * n)))).reshape(3)
+        change = n - m.reshape(3)
+        assert np.max(np.abs((M1[:, k, j, i] - m.reshape(3)) - change)) < 1e-4 * np.max(np.abs(change))
+
+
 @pytest.mark.parametrize("grid", [(24, 16, 3), (32, 32, 4)])
 def test_energy_terms(grid):
     cell = (5e-9, 5e-9, 3e-9)
