@@ -406,6 +406,65 @@ def run_gpu(args, rank, ws):
     return 0
 
 
+def run_sweep(args, rank, ws):
+    """The film size sweep (64x64x4 ... 512x512x8, 200x60x3, plus the
+    512x512x4 and 1024x1024x1 films): per grid the Euler step with the L2
+    flushed before every timed step, the step with the working set left in
+    L2 (one graph of many steps), and one demag evaluation after a flush."""
+    import torch
+    from paper_1406_7459_gb300 import mm, inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = inputs.FILM_SWEEP
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    grids = list(inputs.FILM_SWEEP_GRIDS) + [(512, 512, 4), (1024, 1024, 1)]
+    if args.sweep_grid:
+        grids = [tuple(int(v) for v in g.split("x")) for g in args.sweep_grid.split(",")]
+    K = max(20, min(args.steps, 200))
+
+    def flushed(fn, reps):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        for r in range(reps):
+            flush.fill_(float(r))
+            st[r].record()
+            fn()
+            en[r].record()
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in zip(st, en)) * 1e3
+
+    points = []
+    for grid in grids:
+        n = grid[0] * grid[1] * grid[2]
+        ctx = mm.mm_create(grid, w["cell"], w["Ms"], w["A"], w["Ku"], w["alpha"], w["gamma"])
+        mm.mm_set_m(ctx, torch.from_numpy(inputs.uniform_m(grid, w["Ms"], w["start"]).reshape(-1)).cuda())
+        mm.mm_set_field(ctx, w["H_ext"])
+        mm.mm_step(ctx, max(args.warmup, 3) + 32, w["dt"])
+        torch.cuda.synchronize()
+        step_us = flushed(lambda: mm.mm_step(ctx, 1, w["dt"]), K)
+        mm.mm_step(ctx, 33, w["dt"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mm.mm_step(ctx, 320, w["dt"])
+        e1.record()
+        torch.cuda.synchronize()
+        l2_us = e0.elapsed_time(e1) * 1e3 / 320
+        Md = torch.empty(3 * n, device="cuda")
+        mm.mm_get_m(ctx, Md)
+        Hd = torch.empty_like(Md)
+        demag_us = flushed(lambda: mm.mm_demag_field(ctx, Md, Hd), 50)
+        points.append({"grid": list(grid), "launches_per_step": mm.mm_plan_info(ctx)[1],
+                       "step_us_flushed": step_us, "cells_steps_per_s": n / (step_us * 1e-6),
+                       "step_us_l2_resident": l2_us, "demag_us_flushed": demag_us})
+        mm.mm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps({"workload": "film size sweep, 4 nm cells, Ku 5e2 easy x, alpha 0.02, uniform +x start, "
+                                      "H_ext 2.5e4 A/m at 170 deg, Euler dt 5e-14 s",
+                          "metric": "us per Euler step / per demag evaluation", "dtype": "f32",
+                          "data": "synthetic", "l2": "flushed (256 MiB write) before every flushed timing",
+                          "points": points}))
+    return 0
+
+
 def run_cube(args, rank, ws):
     """Per-step time of the N^3 cube (N = 8..128) beside the paper's Table 1
     (context only: other hardware, other precision, a graphics-API path)."""
@@ -635,11 +694,14 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="film", choices=["film", "cube", "batch", "surrogate"],
+    ap.add_argument("--workload", default="film", choices=["film", "cube", "sweep", "batch", "surrogate"],
                     help="film: the 256x256x4 benchmark line; cube: the N^3 per-step curve; "
+                         "sweep: the film size sweep; "
                          "batch: 512 uneven samples batched vs one at a time; surrogate: the FNO")
     ap.add_argument("--cube-n", default="",
                     help="cube workload: comma-separated subset of the sizes (default all)")
+    ap.add_argument("--sweep-grid", default="",
+                    help="sweep workload: comma-separated grids NXxNYxNZ instead of the sweep's own")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=None,
@@ -654,6 +716,8 @@ def main():
         rc = run_reference(args, rank, ws)
     elif args.workload == "cube":
         rc = run_cube(args, rank, ws)
+    elif args.workload == "sweep":
+        rc = run_sweep(args, rank, ws)
     elif args.workload == "batch":
         rc = run_batch(args, rank, ws)
     elif args.workload == "surrogate":
