@@ -279,8 +279,11 @@ int mm_batch_autotune(mm_batch *b, double dt, int choice[3], float *ms_out);
  * (nz = 1) to H_demag(dM)/Ms.  Width C channels, `modes` retained modes per
  * axis direction (kx < modes, ky < modes or ky >= H - modes), `layers`
  * Fourier layers with GELU between them; BF16 weights and activations with
- * FP32 accumulation (tensor-core mma for the dense contractions), an FP32
- * master copy of the parameters and Adam.  Parameter vector layout:
+ * FP32 accumulation (tcgen05 tensor-core MMAs, accumulator in tensor memory,
+ * for the dense contractions), an FP32 master copy of the parameters and
+ * Adam.  The tensor-core waits are bounded: if one expires, the next call
+ * that synchronises (mm_fno_grad, mm_fno_train_step with a loss) returns
+ * MM_ECUDA.  Parameter vector layout:
  * [P (C*5: three inputs, row/H, column/W), p (C), R_re (L*C*C*2m*m), R_im (same), W (L*C*C), b (L*C),
  *  Q (3*C), q (3)].  x, y, t are (batch, 3, H, W) FP32 device arrays.
  * ------------------------------------------------------------------------ */

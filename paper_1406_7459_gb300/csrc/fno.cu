@@ -9,8 +9,8 @@
 //   the last layer);  y = Q v + q;  S_l keeps kx < m and ky in
 //   {0..m-1} U {H-m..H-1}, with complex weights R_l[c][o] per mode.
 // Dense contractions (the x-direction mode transforms, the channel mixes)
-// run on the tensor cores through a BF16 mma.sync GEMM with FP32
-// accumulators; the small complex transforms along y and the per-mode
+// run on the fifth-generation tensor cores (tcgen05 MMAs with the FP32
+// accumulator in tensor memory, gemm_tc.cuh); the small complex transforms along y and the per-mode
 // channel mix run as FP32 kernels.  Parameters live as an FP32 master copy
 // (Adam moments beside it) and a BF16 copy for the GEMMs.
 #include <cuda_bf16.h>
@@ -25,114 +25,45 @@
 
 #include "../../include/mm.h"
 #include "mm_internal.h"
+#include "gemm_tc.cuh"
 
 using namespace mmk;
 
 namespace mmk {
 
 // ------------------------------------------------------------ BF16 GEMM --
-// C[z](i, j) (+)= alpha * sum_k A[z](i, k) B[z](k, j), A and B BF16 with
-// arbitrary element strides, C FP32.  Batch z: base + z * stride.
-// atomic: accumulate with atomicAdd (split-K over z into one C).
-struct GemmArgs {
-    const __nv_bfloat16* A;
-    const __nv_bfloat16* B;
-    float* C;
-    int M, N, K;
-    long long sam, sak, sbk, sbn, scm, scn;     // element strides
-    long long zA, zB, zC;                        // batch strides
-    float alpha, beta;
-    int atomic;
-};
-
-constexpr int GM = 64, GN = 64, GK = 32;
-
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs a) {
-    __shared__ __nv_bfloat16 As[GM][GK + 8];
-    __shared__ __nv_bfloat16 Bs[GK][GN + 8];
-    const int z = blockIdx.z;
-    const __nv_bfloat16* A = a.A + z * a.zA;
-    const __nv_bfloat16* B = a.B + z * a.zB;
-    float* C = a.C + z * a.zC;
-    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;      // warp tile origin
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < a.K; k0 += GK) {
-        for (int e = threadIdx.x; e < GM * GK; e += blockDim.x) {
-            const int r = e / GK, c = e % GK;
-            const int gi = m0 + r, gk = k0 + c;
-            As[r][c] = (gi < a.M && gk < a.K) ? A[gi * a.sam + gk * a.sak] : zero;
-        }
-        for (int e = threadIdx.x; e < GK * GN; e += blockDim.x) {
-            const int r = e / GN, c = e % GN;
-            const int gk = k0 + r, gj = n0 + c;
-            Bs[r][c] = (gk < a.K && gj < a.N) ? B[gk * a.sbk + gj * a.sbn] : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + gid;
-                af[i][0] = pack_bf16(As[r][kk + 2 * tig], As[r][kk + 2 * tig + 1]);
-                af[i][1] = pack_bf16(As[r + 8][kk + 2 * tig], As[r + 8][kk + 2 * tig + 1]);
-                af[i][2] = pack_bf16(As[r][kk + 2 * tig + 8], As[r][kk + 2 * tig + 9]);
-                af[i][3] = pack_bf16(As[r + 8][kk + 2 * tig + 8], As[r + 8][kk + 2 * tig + 9]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + j * 8 + gid;
-                bf[j][0] = pack_bf16(Bs[kk + 2 * tig][c], Bs[kk + 2 * tig + 1][c]);
-                bf[j][1] = pack_bf16(Bs[kk + 2 * tig + 8][c], Bs[kk + 2 * tig + 9][c]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                        "{%8,%9}, {%0,%1,%2,%3};"
-                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                        : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]),
-                          "r"(bf[j][1]));
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = m0 + wm + i * 16 + gid + (q >= 2 ? 8 : 0);
-                const int c = n0 + wn + j * 8 + 2 * tig + (q & 1);
-                if (r < a.M && c < a.N) {
-                    float* p = C + r * a.scm + c * a.scn;
-                    const float v = a.alpha * acc[i][j][q];
-                    if (a.atomic) atomicAdd(p, v);
-                    else *p = (a.beta != 0.f) ? a.beta * *p + v : v;
-                }
-            }
-}
-
-static cudaError_t gemm(const GemmArgs& g, int batch, cudaStream_t s) {
-    dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM, batch);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+// The tcgen05 kernel of gemm_tc.cuh; the tile width follows N.  A product
+// with fewer rows than a 128-row tile and more columns (the per-sample
+// channel mix, C x C times C x HW) runs as its transpose C^T = B^T A^T.
+template <int BN> static cudaError_t gemm_launch(const GemmArgs& g, int batch, cudaStream_t s) {
+    dim3 grid((g.N + BN - 1) / BN, (g.M + kTcM - 1) / kTcM, batch);
+    k_gemm_tc<BN><<<grid, kTcThreads, gemm_tc_smem<BN>(), s>>>(g);
     return cudaGetLastError();
+}
+
+static cudaError_t gemm(GemmArgs g, int batch, int* err, cudaStream_t s) {
+    g.err = err;
+    if (g.M < kTcM && g.N > g.M) {
+        GemmArgs t = g;
+        t.A = g.B; t.B = g.A; t.M = g.N; t.N = g.M;
+        t.sam = g.sbn; t.sak = g.sbk; t.sbk = g.sak; t.sbn = g.sam;
+        t.scm = g.scn; t.scn = g.scm; t.zA = g.zB; t.zB = g.zA;
+        g = t;
+    }
+    if (g.N <= 32) return gemm_launch<32>(g, batch, s);
+    if (g.N <= 64) return gemm_launch<64>(g, batch, s);
+    return gemm_launch<128>(g, batch, s);
+}
+
+static cudaError_t gemm_configure() {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_tc_smem<32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_tc_smem<64>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gemm_tc_smem<128>());
+    return e;
 }
 
 // ------------------------------------------------------ small FP32 kernels --
@@ -395,6 +326,7 @@ struct mm_fno {
           *du = nullptr, *tmp = nullptr, *dwr = nullptr, *dwi = nullptr;
     __nv_bfloat16 *zb = nullptr, *db16 = nullptr;
     double* dloss = nullptr;
+    int* err = nullptr;           // set by a tensor-core GEMM whose wait expired
 };
 
 static int fno_fail(int code, const char* msg) { return set_error(code, msg); }
@@ -439,7 +371,7 @@ static void fno_free(mm_fno* f) {
     for (auto p : f->vb) cudaFree(p);
     cudaFree(f->whr); cudaFree(f->whi); cudaFree(f->Z); cudaFree(f->acc); cudaFree(f->y); cudaFree(f->dy);
     cudaFree(f->dv); cudaFree(f->du); cudaFree(f->tmp); cudaFree(f->dwr); cudaFree(f->dwi);
-    cudaFree(f->zb); cudaFree(f->db16); cudaFree(f->dloss);
+    cudaFree(f->zb); cudaFree(f->db16); cudaFree(f->dloss); cudaFree(f->err);
 }
 
 extern "C" int mm_fno_create(mm_fno** out, int H, int W, int width, int modes, int layers, int max_batch,
@@ -526,6 +458,9 @@ extern "C" int mm_fno_create(mm_fno** out, int H, int W, int width, int modes, i
         FCU(cudaMalloc(&f->tmp, 4 * act)); FCU(cudaMalloc(&f->db16, 2 * act));
         FCU(cudaMalloc(&f->y, 4LL * max_batch * 3 * f->np)); FCU(cudaMalloc(&f->dy, 4LL * max_batch * 3 * f->np));
         FCU(cudaMalloc(&f->dloss, 8));
+        FCU(cudaMalloc(&f->err, sizeof(int)));
+        FCU(cudaMemset(f->err, 0, sizeof(int)));
+        FCU(gemm_configure());
         return MM_OK;
     }();
     if (rc != MM_OK) {
@@ -580,7 +515,7 @@ static int fno_forward(mm_fno* f, int B, const float* x) {
         g.M = B * C * H; g.N = 2 * m; g.K = W;
         g.sam = W; g.sak = 1; g.sbk = 2 * m; g.sbn = 1; g.scm = 2 * m; g.scn = 1;
         g.alpha = 1.f; g.beta = 0.f;
-        FCU(gemm(g, 1, s));
+        FCU(gemm(g, 1, f->err, s));
         // y modes
         k_ydft<<<grid1((long long)B * C * nmode), 256, 0, s>>>(f->A1[l], 2 * m, H, m, f->Fyre, f->Fyim, 2 * m, B * C,
                                                                 f->vhr[l], f->vhi[l], 1.f, 0);
@@ -598,7 +533,7 @@ static int fno_forward(mm_fno* f, int B, const float* x) {
         g2.M = B * C * H; g2.N = W; g2.K = 2 * m;
         g2.sam = 2 * m; g2.sak = 1; g2.sbk = W; g2.sbn = 1; g2.scm = W; g2.scn = 1;
         g2.alpha = 1.f; g2.beta = 0.f;
-        FCU(gemm(g2, 1, s));
+        FCU(gemm(g2, 1, f->err, s));
         // u += W_l v (per sample: (C x C) . (C x np))
         GemmArgs g3{};
         g3.A = f->wb + (long long)l * C * C; g3.B = f->vb[l]; g3.C = f->u[l];
@@ -606,7 +541,7 @@ static int fno_forward(mm_fno* f, int B, const float* x) {
         g3.sam = C; g3.sak = 1; g3.sbk = np; g3.sbn = 1; g3.scm = np; g3.scn = 1;
         g3.zA = 0; g3.zB = (long long)C * np; g3.zC = (long long)C * np;
         g3.alpha = 1.f; g3.beta = 1.f;
-        FCU(gemm(g3, B, s));
+        FCU(gemm(g3, B, f->err, s));
         // + b_l, activation
         k_add_bias<<<grid1(act), 256, 0, s>>>(f->u[l], f->w + f->ob + (long long)l * C, C, np, B);
         k_act<<<grid1(act), 256, 0, s>>>(f->u[l], f->vb[l + 1], f->vf[l + 1], act, l < L - 1 ? 1 : 0);
@@ -644,7 +579,7 @@ static int fno_backward(mm_fno* f, int B, const float* x, const float* t) {
         g.M = B * C * H; g.N = 2 * m; g.K = W;
         g.sam = W; g.sak = 1; g.sbk = 2 * m; g.sbn = 1; g.scm = 2 * m; g.scn = 1;
         g.alpha = 1.f; g.beta = 0.f;
-        FCU(gemm(g, 1, s));
+        FCU(gemm(g, 1, f->err, s));
         k_ydft<<<grid1((long long)B * C * nmode), 256, 0, s>>>(f->Z, 2 * m, H, m, f->Fyre, f->Fyim, 2 * m, B * C,
                                                                 f->dwr, f->dwi, 1.f / ((float)H * W), 1);
         const long long ro = (long long)l * C * C * nmode;
@@ -660,7 +595,7 @@ static int fno_backward(mm_fno* f, int B, const float* x, const float* t) {
         g2.M = B * C * H; g2.N = W; g2.K = 2 * m;
         g2.sam = 2 * m; g2.sak = 1; g2.sbk = W; g2.sbn = 1; g2.scm = W; g2.scn = 1;
         g2.alpha = 1.f; g2.beta = 1.f;
-        FCU(gemm(g2, 1, s));
+        FCU(gemm(g2, 1, f->err, s));
         float* t2 = f->dv;
         f->dv = f->tmp;
         f->tmp = t2;
@@ -668,6 +603,16 @@ static int fno_backward(mm_fno* f, int B, const float* x, const float* t) {
     k_outer_lift<<<dim3(gx, C * 5), 256, 0, s>>>(f->dv, C, x, H, W, B, f->g + f->oP);
     k_colsum<<<dim3(gx, C), 256, 0, s>>>(f->dv, C, np, B, f->g + f->op);
     FCU(cudaGetLastError());
+    return MM_OK;
+}
+
+// A tensor-core GEMM whose wait expired left its output incomplete; read
+// after the stream has been synchronised.
+static int fno_check_tc(const mm_fno* f) {
+    int e = 0;
+    FCU(cudaMemcpyAsync(&e, f->err, sizeof(int), cudaMemcpyDeviceToHost, f->s));
+    FCU(cudaStreamSynchronize(f->s));
+    if (e) return fno_fail(MM_ECUDA, "a tensor-core GEMM wait timed out; the result is incomplete");
     return MM_OK;
 }
 
@@ -696,6 +641,8 @@ extern "C" int mm_fno_grad(mm_fno* f, int B, const float* x, const float* t, dou
     double l = 0.0;
     FCU(cudaMemcpyAsync(&l, f->dloss, 8, cudaMemcpyDeviceToHost, f->s));
     FCU(cudaStreamSynchronize(f->s));
+    rc = fno_check_tc(f);
+    if (rc != MM_OK) return rc;
     if (loss) *loss = l / (3.0 * B * f->np);
     return MM_OK;
 }
@@ -715,6 +662,8 @@ extern "C" int mm_fno_train_step(mm_fno* f, int B, const float* x, const float* 
         double l = 0.0;
         FCU(cudaMemcpyAsync(&l, f->dloss, 8, cudaMemcpyDeviceToHost, f->s));
         FCU(cudaStreamSynchronize(f->s));
+        rc = fno_check_tc(f);
+        if (rc != MM_OK) return rc;
         *loss = l / (3.0 * B * f->np);
     }
     return MM_OK;
