@@ -283,7 +283,7 @@ int mm_batch_autotune(mm_batch *b, double dt, int choice[3], float *ms_out);
  * for the dense contractions), an FP32 master copy of the parameters and
  * Adam.  The tensor-core waits are bounded: if one expires, the next call
  * that synchronises (mm_fno_grad, mm_fno_train_step with a loss) returns
- * MM_ECUDA.  Parameter vector layout:
+ * MM_ETIMEOUT.  Parameter vector layout:
  * [P (C*5: three inputs, row/H, column/W), p (C), R_re (L*C*C*2m*m), R_im (same), W (L*C*C), b (L*C),
  *  Q (3*C), q (3)].  x, y, t are (batch, 3, H, W) FP32 device arrays.
  * ------------------------------------------------------------------------ */
@@ -310,6 +310,25 @@ int mm_fno_train_step(mm_fno *f, int batch, const float *x, const float *t, floa
  * Synchronises at each refresh.
  */
 int mm_step_surrogate(mm_ctx *ctx, mm_fno *f, int n, double dt, int refresh, double tol, double stats[4]);
+
+/*
+ * mm_gemm_bf16 -- the surrogate's tensor-core GEMM on caller buffers (a
+ * diagnostic entry point; not in the paper):
+ *   C[z] = alpha A[z] B[z] + beta C[z]   (atomic == 0), or
+ *   C[z] += alpha A[z] B[z]              (atomic != 0, atomicAdd per element)
+ * for z < batch.  A (M x K) and B (K x N) are BF16 bit patterns (16-bit
+ * words), C (M x N) FP32; element (i, k) of A[z] is A[z zA + i sam + k sak],
+ * likewise B with (sbk, sbn, zB) and C with (scm, scn, zC).  All device
+ * pointers owned by the caller; runs on cuda_stream (NULL: the default
+ * stream) with tcgen05 MMAs (BF16 inputs, FP32 accumulation in tensor
+ * memory) and synchronises it.  M, N >= 1, K >= 0 (K = 0 gives beta C),
+ * batch in 1..65535, M and N <= 65535 * 128.  Returns MM_EINVAL for a null
+ * pointer or a size out of range, MM_ETIMEOUT if a tensor-core wait expired
+ * (C incomplete), MM_ECUDA for a launch failure.
+ */
+int mm_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, long long sam, long long sak,
+                 long long sbk, long long sbn, long long scm, long long scn, int batch, long long zA, long long zB,
+                 long long zC, float alpha, float beta, int atomic, void *cuda_stream);
 
 /*
  * mm_demag_field_noalloc -- H_demag of M, like mm_demag_field, for callers

@@ -612,7 +612,7 @@ static int fno_check_tc(const mm_fno* f) {
     int e = 0;
     FCU(cudaMemcpyAsync(&e, f->err, sizeof(int), cudaMemcpyDeviceToHost, f->s));
     FCU(cudaStreamSynchronize(f->s));
-    if (e) return fno_fail(MM_ECUDA, "a tensor-core GEMM wait timed out; the result is incomplete");
+    if (e) return fno_fail(MM_ETIMEOUT, "a tensor-core GEMM wait timed out; the result is incomplete");
     return MM_OK;
 }
 
@@ -666,6 +666,35 @@ extern "C" int mm_fno_train_step(mm_fno* f, int B, const float* x, const float* 
         if (rc != MM_OK) return rc;
         *loss = l / (3.0 * B * f->np);
     }
+    return MM_OK;
+}
+
+// error word of mm_gemm_bf16 (one per device image of the library)
+static __device__ int g_gemm_err;
+
+extern "C" int mm_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, long long sam,
+                            long long sak, long long sbk, long long sbn, long long scm, long long scn, int batch,
+                            long long zA, long long zB, long long zC, float alpha, float beta, int atomic,
+                            void* cuda_stream) {
+    if (!C || (K > 0 && (!A || !B))) return fno_fail(MM_EINVAL, "null argument");
+    if (M < 1 || N < 1 || K < 0 || batch < 1 || batch > 65535 || M > 65535LL * kTcM || N > 65535LL * kTcM)
+        return fno_fail(MM_EINVAL, "need M, N in 1..65535*128, K >= 0, batch in 1..65535");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    void* errp = nullptr;
+    FCU(cudaGetSymbolAddress(&errp, g_gemm_err));
+    FCU(gemm_configure());
+    FCU(cudaMemsetAsync(errp, 0, sizeof(int), s));
+    GemmArgs g{};
+    g.A = (const __nv_bfloat16*)A; g.B = (const __nv_bfloat16*)B; g.C = C;
+    g.M = M; g.N = N; g.K = K;
+    g.sam = sam; g.sak = sak; g.sbk = sbk; g.sbn = sbn; g.scm = scm; g.scn = scn;
+    g.zA = zA; g.zB = zB; g.zC = zC;
+    g.alpha = alpha; g.beta = beta; g.atomic = atomic ? 1 : 0;
+    FCU(gemm(g, batch, (int*)errp, s));
+    int e = 0;
+    FCU(cudaMemcpyAsync(&e, errp, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FCU(cudaStreamSynchronize(s));
+    if (e) return fno_fail(MM_ETIMEOUT, "a tensor-core GEMM wait timed out; C is incomplete");
     return MM_OK;
 }
 

@@ -73,6 +73,8 @@ _PROTOS = {
     "mm_fno_grad": (_c_int, [_vp, _c_int, _vp, _vp, ctypes.POINTER(_c_double), _vp]),
     "mm_fno_train_step": (_c_int, [_vp, _c_int, _vp, _vp, ctypes.c_float, ctypes.POINTER(_c_double)]),
     "mm_step_surrogate": (_c_int, [_vp, _vp, _c_int, _c_double, _c_int, _c_double, ctypes.POINTER(_c_double)]),
+    "mm_gemm_bf16": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int] + [ctypes.c_longlong] * 6 +
+                     [_c_int] + [ctypes.c_longlong] * 3 + [ctypes.c_float, ctypes.c_float, _c_int, _vp]),
 }
 
 _lib = None
@@ -415,3 +417,21 @@ def fno_param_dict(flat, width, modes, layers):
         out[name] = flat[o:o + n].reshape(shp)
         o += n
     return out
+
+
+def mm_gemm_bf16(A, B, C, M, N, K, strides, batch=1, batch_strides=(0, 0, 0), alpha=1.0, beta=0.0, atomic=False,
+                 stream=None):
+    """C[z] = alpha A[z] B[z] + beta C[z] (or C[z] += alpha A[z] B[z] with
+    atomic) on the tensor cores.  A, B: bfloat16 CUDA tensors, C: float32
+    CUDA tensor; strides = (sam, sak, sbk, sbn, scm, scn) and batch_strides =
+    (zA, zB, zC) in elements.  Synchronises the stream."""
+    import torch
+    for t, want in ((A, torch.bfloat16), (B, torch.bfloat16), (C, torch.float32)):
+        if t.dtype != want or not t.is_cuda:
+            raise ValueError("A, B must be bfloat16 and C float32 CUDA tensors")
+    sam, sak, sbk, sbn, scm, scn = (int(v) for v in strides)
+    zA, zB, zC = (int(v) for v in batch_strides)
+    _check(lib().mm_gemm_bf16(_vp(A.data_ptr()), _vp(B.data_ptr()), _vp(C.data_ptr()), int(M), int(N), int(K),
+                              sam, sak, sbk, sbn, scm, scn, int(batch), zA, zB, zC, float(alpha), float(beta),
+                              1 if atomic else 0, _vp(_stream_handle(stream))))
+    return C

@@ -69,6 +69,8 @@ def test_null_handling(lib):
     assert lib.mm_set_field(None, None) == -1
     assert lib.mm_sync(None) == -1
     assert lib.mm_create(None, None, None, 1.0, 1.0, 1.0, 1.0, 1.0, None) == -1
+    # mm_gemm_bf16 rejects a null C or null operands before any CUDA call
+    assert lib.mm_gemm_bf16(None, None, None, 4, 4, 4, 4, 1, 4, 1, 4, 1, 1, 0, 0, 0, 1.0, 0.0, 0, None) == -1
 
 
 def test_python_binding_names_match_c_names():
