@@ -99,6 +99,9 @@ static int build_plan(mm_ctx* c) {
     // pass 3: 3 * R3/2 lines of Lx (+ scratch)
     int pairs3 = (int)(32768 / (3 * lx_bytes));
     pairs3 = pairs3 < 1 ? 1 : (pairs3 > 2 ? 2 : pairs3);
+    // small samples: one row pair per tile when two pairs would leave fewer
+    // tiles than two per SM of a 152-SM GPU (the tile is a latency chain)
+    if (pairs3 == 2 && (long long)g.nz * ((g.ny + 3) / 4) < 2 * 152) pairs3 = 1;
     l.r3 = 2 * pairs3;
     if (l.r3 > g.ny + (g.ny & 1)) l.r3 = g.ny + (g.ny & 1);
     l.t3 = 256;
