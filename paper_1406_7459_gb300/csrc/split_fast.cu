@@ -62,8 +62,12 @@ __global__ void __launch_bounds__(YLayout<NY>::THREADS) k_yfwd_fast(Geom g, floa
     }
 }
 
+// NY >= 512: the step B registers of a 32-point DFT would leave one CTA per
+// SM; the bound asks for two
+template <int NY> constexpr int yinv_min_blocks() { return NY >= 512 ? 2 : 1; }
+
 template <int NY>
-__global__ void __launch_bounds__(YLayout<NY>::THREADS) k_yinv_fast(Geom g, float2* __restrict__ S) {
+__global__ void __launch_bounds__(YLayout<NY>::THREADS, yinv_min_blocks<NY>()) k_yinv_fast(Geom g, float2* __restrict__ S) {
     using Lay = YLayout<NY>;
     using F = Fft2<NY>;
     constexpr int P = F::P, Q = F::Q, G = F::G, T = Lay::THREADS, LPC = Lay::LPC, LS = 2 * NY + 2;
