@@ -1,0 +1,57 @@
+"""The byte and flop models behind bench.py's roofline and HBM fractions,
+rebuilt here from the arrays each kernel touches (numpy sizes), at the
+256x256x4 benchmark film (padded 512x512x8)."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+GRID = (256, 256, 4)
+
+
+def _arrays():
+    nx, ny, nz = GRID
+    M = np.zeros((3, nz, ny, nx), np.float32)                     # magnetisation, SoA FP32
+    S = np.zeros((nx + 1, 3, nz, ny), np.complex64)               # x half-spectrum, 3 components
+    Ks = np.zeros((nx + 1, ny + 1, nz + 1, 6), np.float32)        # tensor octant (padded 512 x 512 x 8)
+    Kd = np.zeros((nx + 1, nz, 6, ny + 1), np.float32)            # 2-D spectrum per z offset
+    return M, S, Ks, Kd
+
+
+def test_bytes_of_the_two_kernel_step():
+    M, S, Ks, Kd = _arrays()
+    b = bench.algorithmic_bytes(GRID)
+    # K_A: S in, Sh out, the 2-D spectrum once; K_B: Sh in, S out, M in and out
+    assert b["kA"] == 2 * S.nbytes + Kd.nbytes == 18972768
+    assert b["kB"] == 2 * S.nbytes + 2 * M.nbytes
+    assert b["step2"] == b["kA"] + b["kB"] == 37896288
+    assert b["floor2"] == 2 * M.nbytes + Kd.nbytes == 12632160
+
+
+def test_bytes_of_the_three_pass_model():
+    M, S, Ks, Kd = _arrays()
+    b = bench.algorithmic_bytes(GRID)
+    assert b["pass1"] == M.nbytes + S.nbytes
+    assert b["plane3"] == 2 * S.nbytes + Ks.nbytes
+    assert b["pass3"] == S.nbytes + 2 * M.nbytes
+    assert b["step3"] == b["pass1"] + b["plane3"] + b["pass3"] == 42627192
+    assert b["demag"] == 2 * M.nbytes + 4 * S.nbytes + Ks.nbytes
+
+
+def test_flop_model_and_alu_peak():
+    import math
+    nx, ny, nz = GRID
+    fft = lambda n: 5 * n * math.log2(n)
+    # x: 3 ny nz / 2 row pairs, a forward and an inverse pruned length-2nx
+    # transform each (two length-nx FFTs); y: 3 nz (nx + 1) lines, forward and
+    # inverse pruned length 2ny; z: 9 nz^2 real-by-complex multiply-adds per
+    # (kx, ky) bin; 100 flops per cell for the field and the update
+    want = (2 * (3 * ny * nz // 2) * 2 * fft(nx) + 2 * (3 * nz * (nx + 1)) * 2 * fft(ny)
+            + (nx + 1) * 2 * ny * 9 * nz * nz * 4 + 100 * nx * ny * nz)
+    assert bench.algorithmic_flops(GRID) == want == 291241984
+    assert abs(bench.alu_peak_tflops(2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
