@@ -80,3 +80,39 @@ def test_autotune_keeps_state_and_results():
                           s["gamma"], s["H_ext"], Kt, Lp)
         mine = got[b.offsets[i]:b.offsets[i + 1]].reshape(3, g[2], g[1], g[0])
         assert rel_l2(mine, ref) < 1e-5
+
+
+def test_full_batch_workload_sampled(monkeypatch):
+    """The benchmarked batch at full size: the 512 samples of the batch
+    workload (seed 3), autotuned and stepped as one batch; four of them (the
+    largest among them) checked against their FP64 oracle trajectories and,
+    bit for bit, against single contexts on the same generic kernels."""
+    from paper_1406_7459_gb300 import mm
+    samples = inputs.batch_samples(512, seed=3)
+    b = _make(samples)
+    dt, n = 5e-14, 4
+    choice, _ = mm.mm_batch_autotune(b, dt)
+    mm.mm_batch_step(b, n, dt)
+    out = torch.empty(b.total, device="cuda")
+    mm.mm_batch_get_m(b, out)
+    mm.mm_batch_sync(b)
+    got = out.cpu().numpy()
+    sizes = [s["grid"][0] * s["grid"][1] * s["grid"][2] for s in samples]
+    picks = sorted({0, 255, 511, int(np.argmax(sizes))})
+    monkeypatch.setenv("MM_NO_FAST", "1")
+    for i in picks:
+        s = samples[i]
+        g = s["grid"]
+        mine = got[b.offsets[i]:b.offsets[i + 1]]
+        Kt, Lp = oracle_spectrum(g, s["cell"])
+        ref = L.run_euler(s["M"].astype(np.float64), n, dt, s["cell"], s["Ms"], s["A"], s["Ku"], s["alpha"],
+                          s["gamma"], s["H_ext"], Kt, Lp)
+        assert rel_l2(mine.reshape(3, g[2], g[1], g[0]).astype(np.float64), ref) < 1e-5, (i, g)
+        ctx = mm.mm_create(g, s["cell"], s["Ms"], s["A"], s["Ku"], s["alpha"], s["gamma"])
+        mm.mm_set_field(ctx, s["H_ext"])
+        mm.mm_set_m(ctx, torch.from_numpy(s["M"].reshape(-1)).cuda())
+        mm.mm_step(ctx, n, dt)
+        one = torch.empty(3 * ctx.N, device="cuda")
+        mm.mm_get_m(ctx, one)
+        mm.mm_sync(ctx)
+        assert np.array_equal(one.cpu().numpy(), mine), (i, g, choice)
