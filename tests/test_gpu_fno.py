@@ -50,6 +50,28 @@ def test_fno_forward_and_gradients_match_fp64_oracle():
         assert rel_l2(gd[name], gref[name]) < 5e-2, name
 
 
+def test_fno_forward_at_the_surrogate_size():
+    """The surrogate's network at full size (256 x 256 film, width 32, 16 x 16
+    modes, 4 layers; batch 2) against the FP64 oracle forward pass, with the
+    BF16 tolerance of the small case."""
+    mm = _mm()
+    H, W, C, m, L, B = 256, 256, 32, 16, 4, 2
+    f = mm.mm_fno_create(H, W, C, m, L, max_batch=B, seed=11)
+    flat = mm.mm_fno_get_params(f)
+    rng = np.random.default_rng(1)
+    flat[:] = flat + 0.05 * rng.standard_normal(flat.shape).astype(np.float32)
+    mm.mm_fno_set_params(f, flat)
+    params = mm.fno_param_dict(flat, C, m, L)
+    x = (1e-2 * rng.standard_normal((B, 3, H, W))).astype(np.float32)      # dM / Ms scale
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xd)
+    mm.mm_fno_forward(f, xd, y)
+    yref = OF.forward(params, x.astype(np.float64), m)
+    err = rel_l2(y.cpu().numpy(), yref)
+    print("full-size FNO forward rel L2 %.3e" % err)
+    assert err < 2e-2
+
+
 def _pairs(grid, cell, n_traj, steps, seed):
     """(dM/Ms, H_demag(dM)/Ms) from solver trajectories: random starts,
     alpha 0.02, random fields; increments over 1..8 steps."""
