@@ -13,7 +13,15 @@ Two independent evaluations of Eq. (11)/(12):
 
 Readings: forward transform unnormalised, inverse divided by Lx*Ly*Lz
 (numpy's convention); K = -N with N from ``oracle.tensor``.
+
+``set_workers(n)`` lets ``demag_fft`` use n host threads (for timing the
+oracle on all cores): the transforms then come from ``scipy.fft`` (the same
+pocketfft algorithm numpy uses) with ``workers=n`` and the member-wise
+product runs on n threads over slabs of the padded z axis.  The default is
+one thread and numpy's FFT.
 """
+import concurrent.futures
+
 import numpy as np
 
 from .tensor import COMPONENTS, demag_tensor, tensor_full_offsets
@@ -27,6 +35,26 @@ def _comp(a, b):
     axes = "xyz"
     a, b = sorted((axes[a], axes[b]))
     return _PAIR[(a, b)]
+
+
+_WORKERS = 1
+_POOL = None
+
+
+def set_workers(n):
+    """Host threads for demag_fft (1 = numpy's single-threaded FFT)."""
+    global _WORKERS, _POOL
+    n = max(1, int(n))
+    if n != _WORKERS and _POOL is not None:
+        _POOL.shutdown()
+        _POOL = None
+    _WORKERS = n
+    if n > 1:
+        _POOL = concurrent.futures.ThreadPoolExecutor(max_workers=n)
+
+
+def get_workers():
+    return _WORKERS
 
 
 def default_lengths(grid):
@@ -66,11 +94,25 @@ def demag_fft(M, Kt, L):
     Lx, Ly, Lz = L
     Mp = np.zeros((3, Lz, Ly, Lx))
     Mp[:, :nz, :ny, :nx] = M                                  # step (1)
-    Mt = np.fft.rfftn(Mp, axes=(1, 2, 3))                      # Eq. (14)
+    if _WORKERS == 1:
+        Mt = np.fft.rfftn(Mp, axes=(1, 2, 3))                  # Eq. (14)
+    else:
+        import scipy.fft
+        Mt = scipy.fft.rfftn(Mp, axes=(1, 2, 3), workers=_WORKERS)
     Ht = np.empty_like(Mt)
-    for a in range(3):                                         # Eq. (15)
-        Ht[a] = sum(Kt[_comp(a, b)] * Mt[b] for b in range(3))
-    H = np.fft.irfftn(Ht, s=(Lz, Ly, Lx), axes=(1, 2, 3))      # Eq. (16)
+
+    def product(z0, z1):                                       # Eq. (15)
+        for a in range(3):
+            Ht[a, z0:z1] = sum(Kt[_comp(a, b), z0:z1] * Mt[b, z0:z1] for b in range(3))
+    if _WORKERS == 1 or Lz < 2:
+        product(0, Lz)
+    else:
+        cuts = np.linspace(0, Lz, min(_WORKERS, Lz) + 1).astype(int)
+        list(_POOL.map(lambda i: product(cuts[i], cuts[i + 1]), range(len(cuts) - 1)))
+    if _WORKERS == 1:
+        H = np.fft.irfftn(Ht, s=(Lz, Ly, Lx), axes=(1, 2, 3))  # Eq. (16)
+    else:
+        H = scipy.fft.irfftn(Ht, s=(Lz, Ly, Lx), axes=(1, 2, 3), workers=_WORKERS)
     return H[:, :nz, :ny, :nx]                                 # discard
 
 

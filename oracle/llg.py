@@ -1,8 +1,7 @@
 """Effective field, LLG right-hand side, Euler step, energy (FP64; test
 infrastructure only).
 
-Readings of the paper's Sec. 2 (each listed with its reason in the design
-notes):
+Readings of the paper's Sec. 2:
 * Eq. (1)'s exchange term repeats M_x three times; read as the sum over
   M_x, M_y, M_z.
 * Eq. (3)/(4) omit mu0, which Eq. (5) carries; H_exch = 2A/(mu0 Ms^2) lap M

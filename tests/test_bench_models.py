@@ -55,3 +55,17 @@ def test_flop_model_and_alu_peak():
             + (nx + 1) * 2 * ny * 9 * nz * nz * 4 + 100 * nx * ny * nz)
     assert bench.algorithmic_flops(GRID) == want == 291241984
     assert abs(bench.alu_peak_tflops(2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+
+
+def test_recorded_traffic_only_for_the_captured_kernel_sources(tmp_path):
+    """roofline.traffic comes from an ncu capture committed under profiles/;
+    it is reported only while the step kernels' sources hash to the value
+    recorded with that capture, and is null once they change."""
+    import json
+    f = tmp_path / "traffic.txt"
+    f.write_text(json.dumps({"kA_plane_y_zsum_product": 1.5e7, "kernel_sources_sha16": bench.step_kernel_hash()}))
+    assert bench.recorded_traffic("kA_plane_y_zsum_product", str(f)) == 1.5e7
+    f.write_text(json.dumps({"kA_plane_y_zsum_product": 1.5e7, "kernel_sources_sha16": "0" * 16}))
+    assert bench.recorded_traffic("kA_plane_y_zsum_product", str(f)) is None
+    f.write_text(json.dumps({"kA_plane_y_zsum_product": 1.5e7}))
+    assert bench.recorded_traffic("kA_plane_y_zsum_product", str(f)) is None

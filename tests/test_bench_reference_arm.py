@@ -27,6 +27,10 @@ def test_reference_arm_line():
     assert d["config"] == bench.config_dict()
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    # all host cores as the baseline, one core beside it
+    assert cb["cores"] == bench.host_cores()
+    one = cb["single_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == d["unit"] and one["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

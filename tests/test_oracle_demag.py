@@ -30,6 +30,25 @@ def test_fft_convolution_equals_brute_force(grid):
         assert _rel(Hf, Hb) < 1e-12, L
 
 
+@pytest.mark.parametrize("grid", [(5, 3, 2), (8, 8, 4), (7, 5, 3)])
+def test_threaded_fft_convolution_equals_brute_force(grid):
+    """The multi-threaded demag (scipy transforms, tensor product on a
+    thread pool), used to time the oracle on all host cores, is the same
+    convolution: it must also equal the plain double sum."""
+    M = inputs.random_unit_m(grid, 8.6e5, seed=8).astype(np.float64)
+    octant = T.tensor_octant(grid, CELL)
+    Hb = D.demag_brute(M, octant)
+    L = D.default_lengths(grid)
+    Kt = D.kernel_spectrum(octant, L)
+    D.set_workers(3)
+    try:
+        Hf = D.demag_fft(M, Kt, L)
+    finally:
+        D.set_workers(1)
+    assert D.get_workers() == 1
+    assert _rel(Hf, Hb) < 1e-12
+
+
 def test_too_short_padding_is_rejected():
     octant = T.tensor_octant((4, 4, 1), CELL)
     with pytest.raises(ValueError):
