@@ -99,21 +99,28 @@ def test_adaptive_run_matches_oracle(grid, cell):
 
 
 def test_adaptive_run_step_limit_and_arguments():
+    """A run stopped by its step limit.  The first trial step is small enough
+    that the first two error estimates lie far below tol (0.9 (tol/err)^(1/5)
+    > 5, so the controller's growth clamps at 5 on both sides whatever the
+    FP32 rounding of the estimate): the GPU and the oracle take the same
+    steps dt0, 5 dt0, 25 dt0, all accepted, and the states compare
+    directly, as after one step."""
     grid, cell = GRIDS[0]
     ctx, M = _setup(grid, cell, seed=73)
     Kt, Lp = oracle_spectrum(grid, cell)
-    t_span, dt0, tol = 2e-11, 1e-13, 1e-7
-    ref, _, (acc, rej, nev, t) = L.run_dopri5(M.astype(np.float64), t_span, dt0, tol, 3, cell, MS, A_EX, KU, ALPHA,
-                                              GAMMA, HEXT, Kt, Lp)
-    done, _, st = _mm().mm_run_adaptive(ctx, t_span, dt0, tol, 3)
-    assert not done and st["accepted"] + st["rejected"] == 3 and st["t"] < t_span
-    if st["accepted"] == acc and st["rejected"] == rej:
-        # the step sizes follow the FP32 error estimates (equal to ~1e-4),
-        # so the states compare as changes over nearly equal times
-        assert abs(st["t"] - t) < 1e-3 * t
-        got = _state(ctx, grid)
-        M64 = M.astype(np.float64)
-        assert rel_l2(got - M64, ref - M64) < 5e-3
+    t_span, dt0, tol = 2e-11, 4e-15, 1e-4
+    ref, dt_ref, (acc, rej, nev, t) = L.run_dopri5(M.astype(np.float64), t_span, dt0, tol, 3, cell, MS, A_EX, KU,
+                                                   ALPHA, GAMMA, HEXT, Kt, Lp)
+    assert (acc, rej) == (3, 0) and abs(t - 31 * dt0) < 1e-9 * t
+    done, dt_next, st = _mm().mm_run_adaptive(ctx, t_span, dt0, tol, 3)
+    assert not done and st["accepted"] == 3 and st["rejected"] == 0 and st["evaluations"] == 19
+    assert abs(st["t"] - t) < 1e-9 * t
+    got = _state(ctx, grid)
+    M64 = M.astype(np.float64)
+    assert rel_l2(got, ref) < 1e-6
+    assert rel_l2(got - M64, ref - M64) < 1e-4
+    # the proposed next step follows the third (unclamped) error estimate
+    assert abs(dt_next / dt_ref - 1.0) < 2e-2, (dt_next, dt_ref)
     mm = _mm()
     for bad in ((t_span, -1.0, tol, 10), (t_span, dt0, 0.0, 10), (t_span, dt0, tol, 0), (-1.0, dt0, tol, 10)):
         with pytest.raises(mm.MMError) as ei:
