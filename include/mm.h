@@ -62,6 +62,13 @@ enum {
     MM_INTEGRATOR_RK4 = 2      /* classic Runge-Kutta, fourth order             */
 };
 
+/* How mm_step runs Euler steps (mm_set_step_path). */
+enum {
+    MM_STEP_AUTO = 0,          /* the faster of the two on this device: graphs       */
+    MM_STEP_GRAPH = 1,         /* one launch per kernel per step, replayed from graphs */
+    MM_STEP_PERSISTENT = 2     /* one cooperative launch for many steps            */
+};
+
 /*
  * mm_create -- build a solver context; the tensor set-up happens here, once
  * (Sec. 3: the tensor FFT "carried out at the beginning of simulation").
@@ -175,10 +182,41 @@ int mm_effective_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
  * x R2C, so a film step is two kernels (on power-of-two films the exchange
  * stencil rides in the tensor spectrum) and a thick sample's four; steps are
  * replayed from CUDA graphs of 16 steps (the remainder one step each).
- * n >= 0, dt > 0.
- * Asynchronous: a non-finite result is reported by mm_sync / mm_energy.
+ * On the square power-of-two films the persistent step is built for
+ * (64, 128, 256 wide with nz = 4; 256 x 256 with nz = 1 or 2) the two
+ * kernels' work can instead run as one cooperative launch for up to 1024
+ * steps (plane phase, grid barrier, x-step phase per step; same
+ * arithmetic, same result bits), see mm_set_step_path.  n >= 0, dt > 0.
+ * Asynchronous: a non-finite result is reported by mm_sync / mm_energy, a
+ * grid-barrier wait that gave up (MM_ETIMEOUT, state incomplete) by mm_sync.
  */
 int mm_step(mm_ctx *ctx, int n, double dt);
+
+/*
+ * mm_set_step_path -- choose how mm_step runs Euler steps: MM_STEP_AUTO
+ * (default; the graph step, measured faster on GB300), MM_STEP_GRAPH or
+ * MM_STEP_PERSISTENT.  The persistent step keeps
+ * each block's tensor-spectrum slice, twiddles and M rows in shared memory
+ * across the steps of a launch and replaces the per-step kernel boundaries
+ * by grid barriers (the launch and I/O overhead the paper names in Sec. 4).
+ * Returns MM_EINVAL for an unknown path, MM_EUNSUPPORTED when the
+ * persistent step is asked for but not available for this grid or device.
+ */
+int mm_set_step_path(mm_ctx *ctx, int path);
+
+/* mm_get_step_path -- MM_STEP_PERSISTENT or MM_STEP_GRAPH: how the next
+ * mm_step will run, or a negative error code. */
+int mm_get_step_path(const mm_ctx *ctx);
+
+/*
+ * mm_set_wait_limit -- a diagnostic: the number of polls a grid-barrier
+ * wait of the persistent step makes before it gives up (default 2^20, of
+ * the order of a second).  0 makes every wait that would block give up at
+ * once, which exercises the timeout path: the blocks leave, mm_sync returns
+ * MM_ETIMEOUT and the state is incomplete until the next mm_set_m.
+ * polls >= 0, else MM_EINVAL.
+ */
+int mm_set_wait_limit(mm_ctx *ctx, long long polls);
 
 /*
  * mm_energy -- the energy of Eq. (1) for the current M, summed in FP64:
@@ -350,6 +388,9 @@ int mm_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, lo
  *   Kt_dev    the scaled tensor spectrum exactly as mm_kernel_spectrum
  *             copies it out of a context built for the same grid and cell
  *             (device memory).
+ *   kt_elems  the number of floats in Kt_dev; it must equal
+ *             6*(Lx/2+1)*(Ly/2+1)*(Lz/2+1) for this grid's padded lengths
+ *             (the size mm_kernel_spectrum writes), else MM_EINVAL.
  *   M_dev, H_dev  3*N float32 device arrays, must not overlap.
  *   cuda_stream   stream to run on (NULL = legacy default stream).
  *
@@ -361,8 +402,8 @@ int mm_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, lo
  * every workspace element it reads before reading it, so no clearing is
  * needed.  Asynchronous.  Returns MM_EINVAL, MM_EUNSUPPORTED or MM_ECUDA.
  */
-int mm_demag_field_noalloc(const int grid[3], const float *Kt_dev, const float *M_dev, float *H_dev,
-                           void *cuda_stream);
+int mm_demag_field_noalloc(const int grid[3], const float *Kt_dev, long long kt_elems, const float *M_dev,
+                           float *H_dev, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,11 @@ struct mm_ctx {
     bool spec_valid = false;   // S holds the x half-spectrum of M[cur] (two-kernel step)
     float* dpk[7] = {};        // Dormand-Prince stage slopes (adaptive runs), 3*N each
     unsigned* dperr = nullptr; // error estimate of the last trial step (float bits)
+    PersistFns pf;             // persistent step (square power-of-two films it is built for)
+    bool has_persist = false;  // the persistent step fits this grid and device
+    int step_path = MM_STEP_AUTO;
+    long long wait_limit = kGridWaitLimit;   // polls of a grid-barrier wait
+    GridBar* gbar = nullptr;   // grid-barrier counters of the persistent step
 };
 
 namespace mmk {

@@ -17,15 +17,17 @@
 //
 // Both kernels are launched with programmatic dependent launch.  Before
 // `griddepcontrol.wait` each one only touches data that no kernel of the
-// previous step writes: K_A prefetches its tensor-spectrum slice and the
-// twiddles; K_B prefetches twiddles and its M^n tile (M^n was written two
-// launches earlier, and K_A triggers its dependents only once it has passed
-// its own wait, which orders it after that writer).  Each kernel triggers
+// previous step writes: K_A prefetches the twiddles (its tensor-spectrum
+// slice follows its S lines, after the wait, so that a cold start streams
+// the transforms' inputs first); K_B prefetches twiddles and its M^n tile
+// (M^n was written two launches earlier, and K_A triggers its dependents
+// only once it has passed its own wait, which orders it after that writer).  Each kernel triggers
 // after its last global store (kEarlyTrigger moves K_A's trigger up to
 // its wait), so the next kernel's launch and prologue overlap its tail.
 #pragma once
 #include <cuda_pipeline.h>
 
+#include "bulk_copy.cuh"
 #include "fast_passes.cuh"
 
 namespace mmk {
@@ -59,11 +61,33 @@ template <int NY, int NZ> struct PlaneLayout {
     // [dz*6 + c][ky] as stored, so that consecutive threads (consecutive ky)
     // read consecutive words
     static constexpr int KT_C = KT_FLOATS / 2;            // in float2 units
-    static constexpr int WORK = cmax<NL * ZS, 2 * NL * F::EX>::v;
+    // the lines [line][h][m]; each half (NY slots) is also the swizzled
+    // exchange of its own transform (Fft2::store_sw / load_sw)
+    static constexpr int WORK = NL * ZS;
     static constexpr int TW_OFF = 0, TA_OFF = LY, KT_OFF = LY + NY, WORK_OFF = KT_OFF + ((KT_C + 1) / 2) * 2;
     static constexpr size_t BYTES = sizeof(float2) * (WORK_OFF + WORK);
     static constexpr int THREADS = 2 * NL * F::G;
 };
+
+// Lanes of the calling thread's warp that exist in a block of T threads
+// (the last warp of a block whose size is not a multiple of 32 is partial).
+template <int T> __device__ __forceinline__ unsigned warp_lanes() {
+    if constexpr (T % 32 == 0) return 0xffffffffu;
+    const int base = threadIdx.x & ~31;
+    const int n = T - base < 32 ? T - base : 32;
+    return n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+}
+
+// ta[a Q + t] = W_N^{t a} = tw[2 t a] from the W_2N table tw (both in
+// shared memory; visible to the block after its next barrier).
+template <int N, int Q, int T>
+__device__ __forceinline__ void fill_ta(float2* ta, const float2* tw) {
+#pragma unroll
+    for (int i = threadIdx.x; i < N; i += T) {
+        const int a = i / Q, tt = i - a * Q;
+        ta[i] = tw[2 * tt * a];
+    }
+}
 
 // Direct z sum of one (kx, ky) column for output component a, with
 // M_z' = i M_z and H_z' = i H_z (real couplings, see k_pack2d):
@@ -105,38 +129,28 @@ __device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], Coef coef
     }
 }
 
-template <int NY, int NZ>
-__global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY, NZ>::THREADS <= 512) ? 2 : 1)
-    k_plane_pdl(Geom g, const float* __restrict__ Kd, const float2* __restrict__ S, float2* __restrict__ Sh) {
+// The plane work of K_A for plane kx.  The plane's S lines are on their way
+// into the first halves of the shared lines zb (bulk copies counted on
+// barrier b_s, phase parity par); tw, ta are in shared memory (and visible
+// after the first block barrier here), the 2-D spectrum slice Ks after
+// barrier b_k (phase 0).  2 NL groups of G threads, one per (line, half);
+// threads beyond them (T larger than the plane's own block) only help in
+// the z sum.  Each group transforms its half of a line in place in its own
+// NY slots of zb (warp barriers only); block barriers separate the forward
+// transforms, the z sum (which reads all lines of a column) and the inverse
+// transforms.  Returns false, uniformly over the block, when a copy wait gave
+// up (or ok_in is false); nothing is written to Sh then.
+template <int NY, int NZ, int T>
+__device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, const float2* tw, const float2* ta,
+                                           const float* Ks, float2* zb, uint32_t b_s, uint32_t par, uint32_t b_k,
+                                           float2* __restrict__ Sh) {
     using Lay = PlaneLayout<NY, NZ>;
     using F = Fft2<NY>;
     constexpr int P = F::P, Q = F::Q, G = F::G, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
-    constexpr int T = Lay::THREADS;                       // the launch's block size
-    extern __shared__ __align__(16) float2 sm[];
-    float2* tw = sm + Lay::TW_OFF;
-    float2* ta = sm + Lay::TA_OFF;
-    float* Ks = reinterpret_cast<float*>(sm + Lay::KT_OFF);
-    float2* zb = sm + Lay::WORK_OFF;
-    float2* ex = zb;                                      // aliases zb (barriers separate uses)
-    const int kx = blockIdx.x;
-
-    // prologue: constant data only (twiddles, this kx's slice of the 2-D
-    // spectrum), asynchronous, so that it overlaps the wait and the S load
-#pragma unroll
-    for (int i = threadIdx.x; i < LY / 2; i += T) copy16(tw + 2 * i, g.twy + 2 * i);
-    F::template load_ta<T>(ta, g.twy);
-    {
-        const float* Kp = Kd + (size_t)kx * Lay::KT_FLOATS;
-#pragma unroll
-        for (int i = threadIdx.x; i < Lay::KT_FLOATS / 4; i += T) copy16(Ks + 4 * i, Kp + 4 * i);
-    }
-    __pipeline_commit();
-    pdl_wait();
-    // S of the previous x-step is complete: the next kernel may launch and
-    // run its prologue (it reads nothing this kernel writes before its own wait)
-    if constexpr (kEarlyTrigger) pdl_trigger();
-
-    const float2* plane = S + (size_t)kx * NL * g.Jst;
+    static_assert(T >= Lay::THREADS, "block smaller than the plane's groups");
+    const unsigned lanes = warp_lanes<T>();
+    const bool act = T == Lay::THREADS || threadIdx.x < Lay::THREADS;
+    bool ok = ok_in;
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
     const int line = grp >> 1, h = grp & 1;               // inverse y: a line's halves in one warp
     // forward y: where the groups of a warp can share the half, they do, so
@@ -149,28 +163,34 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         hf = wq & 1;
         lf = (wq >> 1) * GW + s;
     }
+    ok = ok && mbar_wait(b_s, par);
     float2 v[P];
-    if (t < Q) {
-        const float2* src = plane + (size_t)lf * g.Jst;
+    if (ok && act && t < Q) {
+        const float2* src = zb + lf * ZS;                 // both halves' groups read the line
 #pragma unroll
         for (int q = 0; q < P; ++q) v[q] = src[t + Q * q];
     }
-    __pipeline_wait_prior(0);
-    __syncthreads();
-    // forward y (pruned input): odd half pre-multiplied by W_LY^j
-    if (t < Q) {
+    if (__syncthreads_or(!ok)) return false;
+    // forward y (pruned input): odd half pre-multiplied by W_LY^j; the
+    // group's own half-line is its exchange buffer
+    float2* rf = zb + lf * ZS + hf * NY;
+    if (act && t < Q) {
         if (hf) F::odd_input_tab(v, t, tw);
-        F::stepA_tab(v, t, ta, ex + grp * F::EX, false);
+        F::stepA_tab_reg(v, t, ta, false);
+        F::store_sw(v, t, rf);
     }
-    __syncthreads();
+    __syncwarp(lanes);
     float2 w[Q];
-    if (t < P) F::stepB(w, t, ex + grp * F::EX, false);
-    __syncthreads();
-    if (t < P) {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) zb[lf * ZS + hf * NY + t + P * q] = w[q];
+    if (act && t < P) {
+        F::load_sw(w, t, rf);
+        dftp<Q>(w);
     }
-    __syncthreads();
+    __syncwarp(lanes);
+    if (act && t < P) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) rf[t + P * q] = w[q];
+    }
+    if (__syncthreads_or(!mbar_wait(b_k, 0))) return false;   // 2-D spectrum slice
     // z part of the convolution: direct sum over the layers, one (ky)
     // column per task, read and written back by the same thread
 #pragma unroll
@@ -215,16 +235,23 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         }
     }
     __syncthreads();
-    // inverse y (pruned output)
-    if (t < Q) {
+    // inverse y (pruned output), in place in the group's own half-line
+    float2* ri = zb + line * ZS + h * NY;
+    if (act && t < Q) {
 #pragma unroll
-        for (int q = 0; q < P; ++q) v[q] = zb[line * ZS + h * NY + t + Q * q];
+        for (int q = 0; q < P; ++q) v[q] = ri[t + Q * q];
     }
-    __syncthreads();
-    if (t < Q) F::stepA_tab(v, t, ta, ex + grp * F::EX, true);
-    __syncthreads();
-    if (t < P) {
-        F::stepB(w, t, ex + grp * F::EX, true);
+    __syncwarp(lanes);
+    if (act && t < Q) {
+        F::stepA_tab_reg(v, t, ta, true);
+        F::store_sw(v, t, ri);
+    }
+    __syncwarp(lanes);
+    if (act && t < P) {
+        F::load_sw(w, t, ri);
+        dftp<Q>(w);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) w[b].y = -w[b].y;
         if (h) F::odd_output_tab(w, t, tw);
     }
     float2* outp = Sh + (size_t)kx * NL * g.Jst;
@@ -234,14 +261,14 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         for (int q = 0; q < Q; ++q) {
             const float ox = __shfl_down_sync(0xffffffffu, w[q].x, 16);
             const float oy = __shfl_down_sync(0xffffffffu, w[q].y, 16);
-            if (h == 0) outp[(size_t)line * g.Jst + t + P * q] = make_float2(w[q].x + ox, w[q].y + oy);
+            if (act && h == 0) outp[(size_t)line * g.Jst + t + P * q] = make_float2(w[q].x + ox, w[q].y + oy);
         }
     } else {
-        // zb aliases the exchange buffers that step B has just read
-        __syncthreads();
-        if (t < P) {
+        // halves in different warps: through the shared lines
+        __syncwarp(lanes);
+        if (act && t < P) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) zb[line * ZS + h * NY + t + P * q] = w[q];
+            for (int q = 0; q < Q; ++q) ri[t + P * q] = w[q];
         }
         __syncthreads();
 #pragma unroll
@@ -249,6 +276,69 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
             const int l = idx / NY, n = idx % NY;
             outp[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + NY + n]);
         }
+    }
+    return true;
+}
+
+// K_A as a kernel: one kx plane per CTA.
+template <int NY, int NZ>
+__global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY, NZ>::THREADS <= 512) ? 2 : 1)
+    k_plane_pdl(const __grid_constant__ Geom g, const float* __restrict__ Kd, const float2* __restrict__ S, float2* __restrict__ Sh,
+                int* __restrict__ flag) {
+    using Lay = PlaneLayout<NY, NZ>;
+    using F = Fft2<NY>;
+    constexpr int Q = F::Q, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
+    constexpr int T = Lay::THREADS;                       // the launch's block size
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ __align__(8) uint64_t bars[3];             // twiddles, S lines, spectrum slice
+    float2* tw = sm + Lay::TW_OFF;
+    float2* ta = sm + Lay::TA_OFF;
+    float* Ks = reinterpret_cast<float*>(sm + Lay::KT_OFF);
+    float2* zb = sm + Lay::WORK_OFF;
+    const int kx = blockIdx.x;
+    const uint32_t b_tw = smem_addr(&bars[0]), b_s = smem_addr(&bars[1]), b_k = smem_addr(&bars[2]);
+
+    // prologue: bulk copies by one thread.  The twiddles (constant data)
+    // before the wait; after it the plane's S lines (each into the first half
+    // of its shared line), then this kx's slice of the 2-D spectrum, which
+    // only the z sum needs: a cold start streams the transforms' inputs first
+    if (threadIdx.x == 0) {
+        mbar_init(b_tw, 1);
+        mbar_init(b_s, 1);
+        mbar_init(b_k, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(b_tw, LY * sizeof(float2));
+        bulk_g2s(smem_addr(tw), g.twy, LY * sizeof(float2), b_tw);
+    }
+    pdl_wait();
+    // S of the previous x-step is complete: the next kernel may launch and
+    // run its prologue (it reads nothing this kernel writes before its own wait)
+    if constexpr (kEarlyTrigger) pdl_trigger();
+    if (threadIdx.x == 0) {
+        proxy_fence_global();                             // S came from ordinary stores
+        const float2* plane = S + (size_t)kx * NL * g.Jst;
+        mbar_expect_tx(b_s, NL * NY * sizeof(float2));
+#pragma unroll 1
+        for (int l = 0; l < NL; ++l) bulk_g2s(smem_addr(zb + l * ZS), plane + (size_t)l * g.Jst, NY * sizeof(float2), b_s);
+        mbar_expect_tx(b_k, Lay::KT_FLOATS * sizeof(float));
+        bulk_g2s(smem_addr(Ks), Kd + (size_t)kx * Lay::KT_FLOATS, Lay::KT_FLOATS * sizeof(float), b_k);
+    }
+    const bool ok = mbar_wait(b_tw, 0);
+    if (ok) fill_ta<NY, Q, T>(ta, tw);
+    if (!plane_body<NY, NZ, T>(g, kx, ok, tw, ta, Ks, zb, b_s, 0, b_k, Sh)) {
+        // a wait gave up: every thread leaves together, once the copies in
+        // flight have landed (bounded again)
+        if (threadIdx.x == 0) {
+            atomicOr(flag, kFlagTimeout);
+            mbar_wait(b_tw, 0);
+            mbar_wait(b_s, 0);
+            mbar_wait(b_k, 0);
+        }
+        __syncthreads();
+        return;
     }
     if constexpr (!kEarlyTrigger) pdl_trigger();
 }
@@ -275,30 +365,31 @@ template <int N, int R> struct XstepLayout {
     static constexpr int THREADS = cmax<2 * NL * F::G, 128>::v;
 };
 
-// MODE kModeStep: the Euler step (Mout = M^{n+1}, Snext = its x spectrum);
-// kModeHeff: Mout = H_eff of M (Sh from the spectrum with the exchange
-// stencil folded in); kModeDemag: Mout = H_demag (Sh from the plain tensor
-// spectrum, M unused).  Snext and flag are used by the step only.
-template <int N, int R, int MODE>
-__global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
-    k_xstep_pdl(Geom g, LlgCoef cf, const float2* __restrict__ Sh, float2* __restrict__ Snext,
-                const float* __restrict__ M, float* __restrict__ Mout, int* __restrict__ flag) {
+// MODE kModeStep: the Euler step (M^{n+1} replaces M^n in Mt and goes to
+// Mout when Mout is given; Snext = its x spectrum); kModeHeff: Mout = H_eff
+// of M (Sh from the spectrum with the exchange stencil folded in);
+// kModeDemag: Mout = H_demag (Sh from the plain tensor spectrum, Mt unused).
+// Snext and flag are used by the step only.
+//
+// The x-step work for tile `tile` (layer k, rows j0 .. j0 + R - 1): tw, ta
+// (x twiddles) and, except for kModeDemag, the tile's M^n rows Mt
+// (floats [c][row][i]) are in shared memory or on their way there as
+// 16-byte asynchronous copies of this thread (the gather below waits for
+// all of them).  sb stages the tile's rows of Sh, wk the transforms.
+template <int N, int R, int MODE, int T>
+__device__ __forceinline__ void xstep_body(const Geom& g, const LlgCoef& cf, int tile, const float2* tw,
+                                           const float2* ta, float* Mt, float2* sb, float2* wk,
+                                           const float2* __restrict__ Sh, float2* __restrict__ Snext,
+                                           float* __restrict__ Mout, int* __restrict__ flag) {
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
-    constexpr int T = Lay::THREADS;                       // the launch's block size
     constexpr int HM = Lay::HM, HP = Lay::HP, HOFF = Lay::HOFF;
     constexpr int RP = R / 2;                             // row pairs of the tile
-    extern __shared__ __align__(16) float2 sm[];
-    float2* tw = sm + Lay::TW_OFF;
-    float2* ta = sm + Lay::TA_OFF;
-    float* Mt = reinterpret_cast<float*>(sm + Lay::MT_OFF);
-    float2* sb = sm + Lay::SB_OFF;
-    float* Mn = reinterpret_cast<float*>(sm + Lay::SB_OFF);     // new M rows, after sb is consumed
-    float2* wk = sm + Lay::W_OFF;
+    static_assert(T >= 2 * NL * G, "block smaller than the tile's transform groups");
     const int ntj = g.ny / R;
-    const int jt = blockIdx.x % ntj;
-    const int k = blockIdx.x / ntj;
+    const int jt = tile % ntj;
+    const int k = tile / ntj;
     const int j0 = jt * R;
     // 32-bit offsets: the plan admits this kernel only when 3 (nx + 1) nz ny
     // complex values and 3 nx ny nz floats index below 2^31
@@ -307,25 +398,6 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     const int s_c = g.nz * g.Jst, s_kx = 3 * s_c;            // spectrum strides of c and kx
     const int s_base = k * g.Jst + j0;
 
-    // prologue: twiddles and the tile's own M^n rows.  The exchange
-    // stencil of Eq. (4) is folded into the 2-D spectrum as the zero-padded
-    // stencil, so no neighbour rows are needed; what remains of the
-    // free-boundary rule is local (see the field loop below).
-#pragma unroll
-    for (int i = threadIdx.x; i < L / 2; i += T) copy16(tw + 2 * i, g.twx + 2 * i);
-    F::template load_ta<T>(ta, g.twx);
-    if constexpr (MODE != kModeDemag) {
-        constexpr int CH = N / 4;                               // 16-byte chunks per row
-#pragma unroll
-        for (int idx = threadIdx.x; idx < 3 * R * CH; idx += T) {
-            const int ch = idx % CH;
-            const int row = (idx / CH) % R;
-            const int c = idx / (CH * R);
-            copy16(Mt + (c * R + row) * N + 4 * ch, M + c * Nc + k * plane_xy + (j0 + row) * N + 4 * ch);
-        }
-    }
-    __pipeline_commit();
-    pdl_wait();
     // staged half-spectrum of the tile, split by the parity of kx:
     // s4[(c * HP + pos(kx)) * RP + pr] = rows (j0 + 2 pr, j0 + 2 pr + 1) of
     // (c, kx), pos(kx) = (kx & 1) HM + kx / 2, so that the inverse transform
@@ -394,7 +466,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         }
     }
     __syncthreads();
-    // ---- field, LLG, Euler, renormalisation per cell; new rows to Mn.
+    // ---- field, LLG, Euler, renormalisation per cell; new rows to Mt.
     // The spectrum carries the zero-padded exchange stencil; a cell on a
     // free face lacks that neighbour, whose term in Eq. (4) is M(i) itself
     // (zero change), so each missing neighbour adds pexch M(i) / delta^2.
@@ -444,19 +516,22 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
         const float n2 = m[2] + cf.dt * (cf.c1 * p2 + cf.c2 * q2);
         const float s = cf.Ms * rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
         const float o0 = n0 * s, o1 = n1 * s, o2 = n2 * s;
-        if (!isfinite(o0 + o1 + o2)) atomicOr(flag, 1);     // |o| <= Ms when finite
-        Mout[cell] = o0;
-        Mout[Nc + cell] = o1;
-        Mout[2 * Nc + cell] = o2;
-        Mn[(0 * R + r) * N + i] = o0;
-        Mn[(1 * R + r) * N + i] = o1;
-        Mn[(2 * R + r) * N + i] = o2;
+        if (!isfinite(o0 + o1 + o2)) atomicOr(flag, kFlagNonFinite);   // |o| <= Ms when finite
+        if (Mout) {
+            Mout[cell] = o0;
+            Mout[Nc + cell] = o1;
+            Mout[2 * Nc + cell] = o2;
+        }
+        // M^{n+1} replaces M^n in the tile (this thread read its own cell above)
+        Mt[(0 * R + r) * N + i] = o0;
+        Mt[(1 * R + r) * N + i] = o1;
+        Mt[(2 * R + r) * N + i] = o2;
     }
     __syncthreads();
     if constexpr (MODE == kModeStep) {
         // ---- forward x of the new rows (first pass of the next step)
         if (fft_thread && t < Q) {
-            const float* ra = Mn + (size_t)(lc * R + 2 * pr) * N;
+            const float* ra = Mt + (size_t)(lc * R + 2 * pr) * N;
             const float* rb = ra + N;
 #pragma unroll
             for (int q = 0; q < P; ++q) {
@@ -490,6 +565,51 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
             *reinterpret_cast<float4*>(Snext + kx * s_kx + c * s_c + s_base + 2 * p2) = o;
         }
     }
+}
+
+// Fill the tile's M^n rows (floats [c][row][i]) with 16-byte asynchronous
+// copies (committed with the caller's next group).
+template <int N, int R, int T>
+__device__ __forceinline__ void load_mtile(const Geom& g, int tile, const float* __restrict__ M, float* Mt) {
+    constexpr int CH = N / 4;                               // 16-byte chunks per row
+    const int ntj = g.ny / R;
+    const int k = tile / ntj, j0 = (tile % ntj) * R;
+#pragma unroll
+    for (int idx = threadIdx.x; idx < 3 * R * CH; idx += T) {
+        const int ch = idx % CH;
+        const int row = (idx / CH) % R;
+        const int c = idx / (CH * R);
+        copy16(Mt + (c * R + row) * N + 4 * ch, M + (size_t)c * g.N + (size_t)k * N * g.ny + (j0 + row) * N + 4 * ch);
+    }
+}
+
+// K_B as a kernel: one (layer, R rows) tile per CTA.
+template <int N, int R, int MODE>
+__global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
+    k_xstep_pdl(const __grid_constant__ Geom g, const __grid_constant__ LlgCoef cf, const float2* __restrict__ Sh, float2* __restrict__ Snext,
+                const float* __restrict__ M, float* __restrict__ Mout, int* __restrict__ flag) {
+    using Lay = XstepLayout<N, R>;
+    using F = Fft2<N>;
+    constexpr int L = Lay::L;
+    constexpr int T = Lay::THREADS;                       // the launch's block size
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm + Lay::TW_OFF;
+    float2* ta = sm + Lay::TA_OFF;
+    float* Mt = reinterpret_cast<float*>(sm + Lay::MT_OFF);
+    float2* sb = sm + Lay::SB_OFF;
+    float2* wk = sm + Lay::W_OFF;
+    // prologue: twiddles and the tile's own M^n rows, which no kernel of
+    // this step writes.  The exchange stencil of Eq. (4) is folded into the
+    // 2-D spectrum as the zero-padded stencil, so no neighbour rows are
+    // needed; what remains of the free-boundary rule is local (see the field
+    // loop of xstep_body).
+#pragma unroll
+    for (int i = threadIdx.x; i < L / 2; i += T) copy16(tw + 2 * i, g.twx + 2 * i);
+    F::template load_ta<T>(ta, g.twx);
+    if constexpr (MODE != kModeDemag) load_mtile<N, R, T>(g, blockIdx.x, M, Mt);
+    __pipeline_commit();
+    pdl_wait();
+    xstep_body<N, R, MODE, T>(g, cf, blockIdx.x, tw, ta, Mt, sb, wk, Sh, Snext, Mout, flag);
     __syncthreads();
     pdl_trigger();
 }

@@ -44,10 +44,10 @@ cudaError_t configure_step_kernels(const FastStepFns& f) {
 }
 
 cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, const float2* S, float2* Sh,
-                          cudaStream_t s, bool pdl) {
+                          int* flag, cudaStream_t s, bool pdl) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(dim3(g.Hx), f.ta, f.sa, s, attr, pdl);
-    return cudaLaunchKernelEx(&cfg, f.ka, g, Kd, S, Sh);
+    return cudaLaunchKernelEx(&cfg, f.ka, g, Kd, S, Sh, flag);
 }
 
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
@@ -58,8 +58,8 @@ cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c,
 }
 
 cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, int mode, const float* Kd,
-                             float2* S, float2* Sh, const float* M, float* out, cudaStream_t s) {
-    cudaError_t e = launch_step_a(g, f, Kd, S, Sh, s, true);
+                             float2* S, float2* Sh, const float* M, float* out, int* flag, cudaStream_t s) {
+    cudaError_t e = launch_step_a(g, f, Kd, S, Sh, flag, s, true);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, attr, true);
@@ -71,7 +71,7 @@ cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef&
 // waits on griddepcontrol before reading what the predecessor wrote).
 cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
                             const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
-    cudaError_t e = launch_step_a(g, f, g.Kd, S, Sh, s, pdl);
+    cudaError_t e = launch_step_a(g, f, g.Kd, S, Sh, flag, s, pdl);
     if (e != cudaSuccess) return e;
     return launch_step_b(g, f, c, Sh, S, M, Mout, flag, s, pdl);
 }

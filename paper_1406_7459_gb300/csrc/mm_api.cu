@@ -12,6 +12,7 @@
 #include <mutex>
 #include <new>
 
+#include "bulk_copy.cuh"
 #include "ctx_internal.h"
 
 using namespace mmk;
@@ -163,6 +164,7 @@ static int build_plan(mm_ctx* c) {
         c->has_ss = !ok && l.split && l.fs2 && s.kb[kModeStep] && g.ny % s.rb == 0 && s.sb <= smem_cap &&
                     3.0 * g.Hx * g.nz * g.Jst < (double)INT_MAX && 3.0 * g.N < (double)INT_MAX;
         if (c->has_ss) s.ka = nullptr;
+        c->has_persist = ok && persist_lookup(g.nx, g.ny, g.nz, s.rb, &c->pf);
     }
     if (!c->has_fs && !c->has_ss && !l.fx) {
         c->has_gx = true;
@@ -230,6 +232,7 @@ static void release(mm_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->Edev);
     cudaFree(c->tw);
+    cudaFree(c->gbar);
     if (c->cap) cudaStreamDestroy(c->cap);
 }
 
@@ -309,6 +312,12 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         g.Kd0 = c->Kd0;
         CU(configure_pass_kernels(g, c->l));
         if (c->has_fs || c->has_ss) CU(configure_step_kernels(c->fs));
+        if (c->has_persist) {
+            bool usable = false;
+            CU(persist_configure(g, c->fs.rb, &c->pf, &usable));
+            c->has_persist = usable;
+            if (usable) CU(persist_alloc_bar(&c->gbar));
+        }
 
         // tensor set-up in FP64
         const int L[3] = {g.Lx, g.Ly, g.Lz};
@@ -434,7 +443,8 @@ int mmk::run_passes(mm_ctx* c, int mode, const float* M, float* out, double dt, 
         // variant of its x-step kernel (where the plane kernel runs at most
         // 512 threads: larger ones are register-starved, and the three-pass
         // plane kernel serves them better)
-        CU(launch_field_pdl(c->g, c->fs, cf, mode, mode == kModeDemag ? c->Kd0 : c->Kd, c->S, c->Sh, M, out, s));
+        CU(launch_field_pdl(c->g, c->fs, cf, mode, mode == kModeDemag ? c->Kd0 : c->Kd, c->S, c->Sh, M, out, c->flag,
+                            s));
         return MM_OK;
     }
     if (c->has_ss && (mode == kModeDemag || mode == kModeHeff)) {
@@ -547,6 +557,39 @@ static int ensure_spectrum(mm_ctx* c) {
     return MM_OK;
 }
 
+// Steps per launch of the persistent step.
+constexpr int kPersistChunk = 1024;
+
+// mm_step takes the persistent kernel for Euler steps only when asked to
+// (MM_STEP_PERSISTENT): on GB300 the two-kernel graph step is faster (the
+// persistent kernel's 384-thread blocks, two per SM, cap both phases at 80
+// registers, which the x-step phase exceeds).
+static bool uses_persist(const mm_ctx* c) {
+    return c->has_persist && c->method == MM_INTEGRATOR_EULER && c->step_path == MM_STEP_PERSISTENT;
+}
+
+extern "C" int mm_set_step_path(mm_ctx* c, int path) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    if (path != MM_STEP_AUTO && path != MM_STEP_GRAPH && path != MM_STEP_PERSISTENT)
+        return fail(MM_EINVAL, "unknown step path %d", path);
+    if (path == MM_STEP_PERSISTENT && !c->has_persist)
+        return fail(MM_EUNSUPPORTED, "no persistent step for this grid and device");
+    c->step_path = path;
+    return MM_OK;
+}
+
+extern "C" int mm_get_step_path(const mm_ctx* c) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    return uses_persist(c) ? MM_STEP_PERSISTENT : MM_STEP_GRAPH;
+}
+
+extern "C" int mm_set_wait_limit(mm_ctx* c, long long polls) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    if (polls < 0) return fail(MM_EINVAL, "polls must be >= 0");
+    c->wait_limit = polls;
+    return MM_OK;
+}
+
 extern "C" int mm_step(mm_ctx* c, int n, double dt) {
     if (!c) return fail(MM_EINVAL, "null context");
     if (n < 0) return fail(MM_EINVAL, "n must be >= 0");
@@ -554,6 +597,19 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
     if (n == 0) return MM_OK;
     int rc = ensure_spectrum(c);
     if (rc != MM_OK) return rc;
+    if (uses_persist(c)) {
+        // n steps per launch (in chunks, so that one launch stays short)
+        const LlgCoef cf = make_coef(c, dt);
+        for (int s = 0; s < n;) {
+            const int m = std::min(n - s, kPersistChunk);
+            const int p = c->cur, q = (p + m) & 1;
+            CU(launch_persist(c->g, c->pf, cf, c->Kd, c->S, c->Sh, c->Mbuf[p], c->Mbuf[q], m, c->flag, c->gbar,
+                              c->wait_limit, c->stream));
+            c->cur = q;
+            s += m;
+        }
+        return MM_OK;
+    }
     for (int s = 0; s < n;) {
         const int p = c->cur;
         if (c->use_graphs) {
@@ -578,6 +634,7 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
 static int read_flag(mm_ctx* c) {
     int f = 0;
     CU(cudaMemcpy(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f & kFlagTimeout) return fail(MM_ETIMEOUT, "a device-side wait gave up; the state is incomplete");
     if (f) return fail(MM_ENONFINITE, "a step produced a non-finite magnetisation");
     return MM_OK;
 }
@@ -655,7 +712,7 @@ extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsig
                 // pass 1 alone (the two-kernel step folds it into K_B), then K_A, K_B
                 CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
                 CU(cudaEventRecord(ev[1], c->stream));
-                CU(launch_step_a(c->g, c->fs, c->Kd, c->S, c->Sh, c->stream, false));
+                CU(launch_step_a(c->g, c->fs, c->Kd, c->S, c->Sh, c->flag, c->stream, false));
                 CU(cudaEventRecord(ev[2], c->stream));
                 CU(launch_step_b(c->g, c->fs, cf, c->Sh, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag,
                                  c->stream, false));
@@ -710,8 +767,8 @@ __global__ void k_noalloc_twiddles(int Lx, int Ly, int Lz, float2* tw) {
     tw[m] = make_float2((float)c, (float)s);
 }
 
-extern "C" int mm_demag_field_noalloc(const int grid[3], const float* Kt_dev, const float* M_dev, float* H_dev,
-                                      void* cuda_stream) {
+extern "C" int mm_demag_field_noalloc(const int grid[3], const float* Kt_dev, long long kt_elems,
+                                      const float* M_dev, float* H_dev, void* cuda_stream) {
     if (!grid || !Kt_dev || !M_dev || !H_dev) return fail(MM_EINVAL, "null argument");
     for (int a = 0; a < 3; ++a)
         if (grid[a] < 1) return fail(MM_EINVAL, "grid[%d] = %d < 1", a, grid[a]);
@@ -731,6 +788,10 @@ extern "C" int mm_demag_field_noalloc(const int grid[3], const float* Kt_dev, co
         return fail(MM_EUNSUPPORTED,
                     "grid %dx%dx%d needs %zu bytes of workspace; the static workspace holds %zu bytes",
                     grid[0], grid[1], grid[2], need * sizeof(float2), kNoAllocComplex * sizeof(float2));
+    const long long kt_need = 6LL * g.Hx * g.Hy * g.Hz;
+    if (kt_elems != kt_need)
+        return fail(MM_EINVAL, "Kt holds %lld floats; the spectrum of grid %dx%dx%d has %lld", kt_elems, grid[0],
+                    grid[1], grid[2], kt_need);
     int dev = 0;
     CU(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(MM_EUNSUPPORTED, "device ordinal %d out of range", dev);

@@ -150,7 +150,7 @@ bool fast_lookup_plane_nz8(int ny, FastFns* f);
 // the step and H_eff, plain for H_demag); K_B = inverse x + LLG + forward x
 // from Sh into S, or its field-only variants.
 struct FastStepFns {
-    void (*ka)(Geom, const float*, const float2*, float2*) = nullptr;
+    void (*ka)(Geom, const float*, const float2*, float2*, int*) = nullptr;
     int ta = 0;
     size_t sa = 0;
     // x-step kernels by Pass3Mode: demag field, effective field, Euler step
@@ -167,12 +167,34 @@ cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& 
                             const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 cudaError_t configure_step_kernels(const FastStepFns& f);
 cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, const float2* S, float2* Sh,
-                          cudaStream_t s, bool pdl);
+                          int* flag, cudaStream_t s, bool pdl);
 // The two-kernel evaluation of H_demag (mode kModeDemag, plain 2-D spectrum
 // Kd0) or H_eff (kModeHeff, exchange-folded Kd) of M into out, after
 // launch_pass1 has formed S from M.
 cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, int mode, const float* Kd,
-                             float2* S, float2* Sh, const float* M, float* out, cudaStream_t s);
+                             float2* S, float2* Sh, const float* M, float* out, int* flag, cudaStream_t s);
+// Persistent Euler step (step_persist.cu): K_A phase, grid barrier, K_B
+// phase for n steps in one cooperative launch, for the square power-of-two
+// films it is instantiated for.
+struct GridBar;
+struct PersistFns {
+    void (*k)(Geom, LlgCoef, const float*, float2*, float2*, const float*, float*, int, int*, GridBar*,
+              long long) = nullptr;
+    int t = 0, grid = 0;
+    size_t smem = 0;
+};
+bool persist_lookup(int nx, int ny, int nz, int R, PersistFns* f);
+cudaError_t persist_configure(const Geom& g, int R, PersistFns* f, bool* usable);
+cudaError_t persist_alloc_bar(GridBar** gb);
+// n steps from M^n (Min, with S its x spectrum) to M^{n+n} in Mout; S ends as
+// the spectrum of the new state.  limit: polls a grid-barrier wait makes
+// before it gives up (kFlagTimeout in *flag).
+cudaError_t launch_persist(const Geom& g, const PersistFns& f, const LlgCoef& c, const float* Kd, float2* S,
+                           float2* Sh, const float* Min, float* Mout, int n, int* flag, GridBar* gb, long long limit,
+                           cudaStream_t s);
+// Default poll limit of a grid-barrier wait (of the order of a second).
+constexpr long long kGridWaitLimit = 1LL << 20;
+
 // Thick-sample step / field: launch_fast_split with Kt, then the x-step
 // kernel of mode `mode` in place on S (S -> S, M -> out).
 cudaError_t launch_split_xstep(const Geom& g, const FastSplitFns& f2, const FastStepFns& fs, const LlgCoef& c,

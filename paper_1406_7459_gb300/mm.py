@@ -23,6 +23,10 @@ MM_ETIMEOUT = -5
 MM_EUNSUPPORTED = -6
 MM_ELIMIT = -7
 
+MM_STEP_AUTO = 0
+MM_STEP_GRAPH = 1
+MM_STEP_PERSISTENT = 2
+
 MM_INTEGRATOR_EULER = 0
 MM_INTEGRATOR_HEUN = 1
 MM_INTEGRATOR_RK4 = 2
@@ -40,6 +44,9 @@ _PROTOS = {
     "mm_demag_field": (_c_int, [_vp, _vp, _vp]),
     "mm_effective_field": (_c_int, [_vp, _vp, _vp]),
     "mm_step": (_c_int, [_vp, _c_int, _c_double]),
+    "mm_set_step_path": (_c_int, [_vp, _c_int]),
+    "mm_get_step_path": (_c_int, [_vp]),
+    "mm_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
     "mm_run_adaptive": (_c_int, [_vp, _c_double, ctypes.POINTER(_c_double), _c_double, _c_int,
                                  ctypes.POINTER(_c_double)]),
     "mm_energy": (_c_int, [_vp, ctypes.POINTER(_c_double)]),
@@ -50,7 +57,7 @@ _PROTOS = {
     "mm_kernel_spectrum": (_c_int, [_vp, _vp]),
     "mm_time_passes": (_c_int, [_vp, _c_int, _c_double, _vp, ctypes.c_ulonglong,
                                 ctypes.POINTER(ctypes.c_float)]),
-    "mm_demag_field_noalloc": (_c_int, [ctypes.POINTER(_c_int), _vp, _vp, _vp, _vp]),
+    "mm_demag_field_noalloc": (_c_int, [ctypes.POINTER(_c_int), _vp, ctypes.c_longlong, _vp, _vp, _vp]),
     "mm_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_double),
                                  ctypes.POINTER(_c_double), ctypes.POINTER(_c_double),
                                  ctypes.POINTER(_c_double), ctypes.POINTER(_c_double),
@@ -199,6 +206,18 @@ def mm_step(ctx, n, dt):
     _check(lib().mm_step(ctx.handle, int(n), float(dt)))
 
 
+def mm_set_step_path(ctx, path):
+    _check(lib().mm_set_step_path(ctx.handle, int(path)))
+
+
+def mm_get_step_path(ctx):
+    return _check(lib().mm_get_step_path(ctx.handle))
+
+
+def mm_set_wait_limit(ctx, polls):
+    _check(lib().mm_set_wait_limit(ctx.handle, int(polls)))
+
+
 def mm_run_adaptive(ctx, t_span, dt, tol, max_steps=100000):
     """Adaptive Dormand-Prince run over t_span seconds.  Returns (complete,
     dt_next, stats) with stats = dict(accepted, rejected, evaluations, t);
@@ -261,7 +280,8 @@ def mm_demag_field_noalloc(grid, Kt, M, H, stream=None):
     the device copy of mm_kernel_spectrum for the same grid and cell."""
     g = (ctypes.c_int * 3)(*[int(v) for v in grid])
     n = 3 * int(grid[0]) * int(grid[1]) * int(grid[2])
-    _check(lib().mm_demag_field_noalloc(g, _vp(_ptr(Kt)), _vp(_ptr(M, n)), _vp(_ptr(H, n)),
+    kt_elems = int(Kt.numel() if hasattr(Kt, "numel") else Kt.size)
+    _check(lib().mm_demag_field_noalloc(g, _vp(_ptr(Kt)), kt_elems, _vp(_ptr(M, n)), _vp(_ptr(H, n)),
                                         _vp(_stream_handle(stream))))
     return H
 

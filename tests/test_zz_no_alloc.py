@@ -22,7 +22,9 @@ def _gpu():
 
 
 @pytest.mark.parametrize("grid,cell", [((256, 256, 4), (4e-9, 4e-9, 4e-9)),
-                                       ((48, 40, 3), (5e-9, 4e-9, 3e-9))])
+                                       ((48, 40, 3), (5e-9, 4e-9, 3e-9)),
+                                       # thick: the split y/z pass with row stride Ly
+                                       ((32, 32, 16), (4e-9, 4e-9, 4e-9))])
 def test_noalloc_matches_mm_demag_field_on_two_calls(grid, cell):
     from paper_1406_7459_gb300 import mm
     ctx = mm.mm_create(grid, cell, MS, 1.3e-11, 0.0, 0.5, inputs.GAMMA0)
@@ -40,6 +42,21 @@ def test_noalloc_matches_mm_demag_field_on_two_calls(grid, cell):
         assert np.all(np.isfinite(a))
         assert rel_l2(a, b) < 1e-5
         assert rel_max(a, b) < 1e-5
+
+
+def test_noalloc_rejects_a_spectrum_of_the_wrong_size():
+    from paper_1406_7459_gb300 import mm
+    grid, cell = (48, 40, 3), (5e-9, 4e-9, 3e-9)
+    ctx = mm.mm_create(grid, cell, MS, 1.3e-11, 0.0, 0.5, inputs.GAMMA0)
+    (Lx, Ly, Lz), _ = mm.mm_plan_info(ctx)
+    n_kt = (Lx // 2 + 1) * (Lz // 2 + 1) * (Ly // 2 + 1) * 6
+    Kt = torch.zeros(n_kt - 6, dtype=torch.float32, device="cuda")   # a smaller grid's size
+    M = torch.zeros(3 * 48 * 40 * 3, device="cuda")
+    H = torch.zeros_like(M)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_demag_field_noalloc(grid, Kt, M, H)
+    assert e.value.code == mm.MM_EINVAL
+    assert "Kt" in str(e.value)
 
 
 def test_noalloc_rejects_grids_beyond_its_workspace():
