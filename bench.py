@@ -579,17 +579,24 @@ def run_batch(args, rank, ws):
     choice, tune_ms = mm.mm_batch_autotune(b, dt)
     cells = mm.mm_batch_cells(b)
     K = max(10, min(args.steps, 200))
-    mm.mm_batch_step(b, max(args.warmup, 3), dt)
-    barrier(ws)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    mm.mm_batch_step(b, K, dt)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier(ws)
-    mm.mm_batch_sync(b)
-    batch_ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+    path_ms = {}
+    for name, path in (("graph", mm.MM_STEP_GRAPH), ("persistent", mm.MM_STEP_PERSISTENT)):
+        mm.mm_batch_set_path(b, path)
+        mm.mm_batch_step(b, max(args.warmup, 3), dt)
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record()
+        mm.mm_batch_step(b, K, dt)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        mm.mm_batch_sync(b)
+        path_ms[name] = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+    batch_ms = path_ms["graph"]
+    by = batch_bytes([s["grid"] for s in samples])
+    by = {k: sum_over_ranks(float(v), ws) for k, v in by.items()}
+    peak, peak_kind = measured_peaks()
     cells = int(sum_over_ranks(float(cells), ws))
     # the same samples, one context each, stepped one after another
     ctxs = []
@@ -617,6 +624,15 @@ def run_batch(args, rank, ws):
                           "n_gpus": ws, "sharding": "round-robin samples per rank, no data-path collective",
                           "cells": cells, "batched_ms_per_step": batch_ms,
                           "batched_cells_steps_per_s": cells / (batch_ms * 1e-3),
+                          "paths": {name: {"ms_per_step": ms, "cells_steps_per_s": cells / (ms * 1e-3),
+                                           "algorithmic_bytes_per_step": by[name],
+                                           "hbm_gbs": by[name] / (ms * 1e-3) / 1e9,
+                                           "hbm_frac": by[name] / (ms * 1e-3) / 1e9 / peak}
+                                    for name, ms in path_ms.items()},
+                          "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
+                          "byte_model": "graph: per sample 36N + 96X + 24Ks (x R2C, plane, update); "
+                                        "persistent: 24N + 96X + 24Ks (x R2C fused into the update); "
+                                        "X = (Lx/2+1) ny nz, Ks = (Lx/2+1)(Ly/2+1)(Lz/2+1), FP32",
                           "one_context_at_a_time_ms_per_step": single_ms,
                           "one_context_at_a_time_cells_steps_per_s": cells / (single_ms * 1e-3),
                           "batching_gain": single_ms / batch_ms,
@@ -625,6 +641,38 @@ def run_batch(args, rank, ws):
                           "autotune_ms_per_candidate": tune_ms,
                           "l2": "working set larger than L2; steps back to back"}))
     return 0
+
+
+def padded_length(n):
+    """The plan's padded FFT length: 1 for n = 1, 2n for a power of two,
+    else the smallest 2^a 3^b 5^c >= 2n - 1."""
+    if n == 1:
+        return 1
+    if n & (n - 1) == 0:
+        return 2 * n
+    m = 2 * n - 1
+    while True:
+        r = m
+        for p in (2, 3, 5):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return m
+        m += 1
+
+
+def batch_bytes(grids):
+    """Algorithmic bytes of one batch step summed over the samples, for the
+    graph path (three passes) and the persistent path (x R2C fused)."""
+    tot = {"graph": 0, "persistent": 0}
+    for nx, ny, nz in grids:
+        Lx, Ly, Lz = padded_length(nx), padded_length(ny), padded_length(nz)
+        N = nx * ny * nz
+        X = (Lx // 2 + 1) * ny * nz
+        Ks = (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1)
+        tot["graph"] += 36 * N + 96 * X + 24 * Ks
+        tot["persistent"] += 24 * N + 96 * X + 24 * Ks
+    return tot
 
 
 def run_surrogate(args, rank, ws):

@@ -283,7 +283,10 @@ int mm_time_passes(mm_ctx *ctx, int reps, double dt, void *flush, unsigned long 
  * size slowness on launch overhead, which batching removes).  Sample s has
  * its own grid (nz <= 4), cell, material, field and tensor spectrum; every
  * call of mm_batch_step advances all samples by forward-Euler steps of the
- * same dt, with three batched kernels per step replayed from a CUDA graph.
+ * same dt, with three batched kernels per step replayed from a CUDA graph,
+ * or (mm_batch_set_path MM_STEP_PERSISTENT) as one cooperative launch for up
+ * to 1024 steps whose blocks take (sample, tile) items from a work queue per
+ * pass, the passes separated by bounded grid barriers (same arithmetic).
  * M arrays of a batch are the samples' SoA blocks back to back (sample s
  * starts at float offset sum_{t<s} 3 N_t).
  * ------------------------------------------------------------------------ */
@@ -300,7 +303,15 @@ int mm_batch_set_field(mm_batch *b, const double *H_ext); /* 3n doubles, A/m */
 int mm_batch_set_m(mm_batch *b, const float *M);          /* host or device; synchronises */
 int mm_batch_get_m(mm_batch *b, float *M);                /* host or device; synchronises */
 int mm_batch_step(mm_batch *b, int n, double dt);         /* asynchronous */
-int mm_batch_sync(mm_batch *b);                           /* MM_ENONFINITE if any step failed */
+/* MM_ENONFINITE if any step failed, MM_ETIMEOUT if a grid-barrier wait of the
+ * persistent step gave up (the state is then incomplete until mm_batch_set_m) */
+int mm_batch_sync(mm_batch *b);
+/* MM_STEP_AUTO (default: the graph step), MM_STEP_GRAPH or MM_STEP_PERSISTENT;
+ * MM_EUNSUPPORTED if the persistent step's blocks cannot all be resident. */
+int mm_batch_set_path(mm_batch *b, int path);
+/* Polls a grid-barrier wait of the persistent batch step makes before it gives
+ * up (default 2^20; 0: at once, to exercise the timeout path).  polls >= 0. */
+int mm_batch_set_wait_limit(mm_batch *b, long long polls);
 long long mm_batch_cells(const mm_batch *b);              /* total cells, or -1 */
 /*
  * mm_batch_autotune -- time the candidate tile shapes (rows per CTA of the

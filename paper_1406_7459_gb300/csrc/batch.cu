@@ -7,8 +7,12 @@
 // batched kernel per pass covers the tiles of every sample, each CTA
 // finding its (sample, tile) in a prefix table over a per-sample
 // descriptor array, and the three launches of a step replay from one CUDA
-// graph.  The tile shapes (rows per CTA in the x passes, threads per CTA)
-// come from an autotuner that times candidate shapes on the batch itself.
+// graph.  Or (MM_STEP_PERSISTENT) one cooperative launch runs many steps:
+// its blocks take (sample, tile) items from a work queue per pass, passes
+// separated by bounded grid barriers, the x R2C of the next step fused into
+// the update pass.  The tile shapes (rows per CTA in the x passes, threads
+// per CTA) come from an autotuner that times candidate shapes on the batch
+// itself.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,6 +23,8 @@
 #include <vector>
 
 #include "../../include/mm.h"
+#include "bulk_copy.cuh"
+#include "grid_sync.cuh"
 #include "pass_bodies.cuh"
 #include "plane_kernel.cuh"
 
@@ -76,7 +82,65 @@ __global__ void __launch_bounds__(256) k_batch_pass3(const BatchDesc* __restrict
                           blockIdx.x - __ldg(pre + s));
 }
 
+__device__ __forceinline__ void batch_plane_tile(const BatchDesc& b, int tile) {
+    const int nl = 3 * b.g.nz;
+    switch (b.g.Lz) {
+        case 1: plane_body<1>(b.g, nl, b.S, tile); break;
+        case 4: plane_body<4>(b.g, nl, b.S, tile); break;
+        case 5: plane_body<5>(b.g, nl, b.S, tile); break;
+        default: plane_body<8>(b.g, nl, b.S, tile); break;
+    }
+}
+
+// n steps of every sample in one cooperative launch.  Work queue 0 holds
+// the pass-1 tiles (the x R2C of the starting state; only when the spectra
+// are not already those of that state), queue 1 the plane tiles, queue 2
+// the update tiles, which also form the next step's x spectra (kModeStepX,
+// in place: a tile reads exactly the spectrum entries it writes).  The
+// state goes M[par0] -> M[par0 ^ 1] -> ...  A grid-barrier wait that runs
+// out of polls sets kFlagTimeout.
+__global__ void __launch_bounds__(256) k_batch_persist(const BatchDesc* __restrict__ d, const int* __restrict__ pre,
+                                                        int ns, int t1, int t2, int t3, int par0, int nsteps,
+                                                        float dt, int first_x, int* __restrict__ flag,
+                                                        GridBar* __restrict__ gb, long long limit) {
+    __shared__ int slot;
+    const int P = ns + 1;
+    unsigned bar = 0;
+    bool ok = true;
+    if (first_x) {
+        for (int i; (i = queue_next(gb, 0, t1, 0, &slot)) >= 0;) {
+            const int s = find_sample(pre, ns, i);
+            const BatchDesc& b = d[s];
+            pass1_body(b.g, b.r1, b.r1 / 2, par0 ? b.M1 : b.M0, b.S, i - __ldg(pre + s));
+        }
+        ok = grid_sync(gb, bar++, limit);
+    }
+    for (int st = 0; ok && st < nsteps; ++st) {
+        const int par = (par0 + st) & 1;
+        for (int i; (i = queue_next(gb, 1, t2, st, &slot)) >= 0;) {
+            const int s = find_sample(pre + P, ns, i);
+            batch_plane_tile(d[s], i - __ldg(pre + P + s));
+        }
+        ok = grid_sync(gb, bar++, limit);
+        if (!ok) break;
+        for (int i; (i = queue_next(gb, 2, t3, st, &slot)) >= 0;) {
+            const int s = find_sample(pre + 2 * P, ns, i);
+            const BatchDesc& b = d[s];
+            LlgCoef cf = b.cf;
+            cf.dt = dt;
+            pass3_body<kModeStepX>(b.g, b.r3, 3 * b.r3 / 2, cf, b.S, par ? b.M1 : b.M0, par ? b.M0 : b.M1, flag,
+                                   i - __ldg(pre + 2 * P + s), b.S);
+        }
+        if (st + 1 < nsteps) ok = grid_sync(gb, bar++, limit);
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(flag, kFlagTimeout);
+    grid_exit(gb);
+}
+
 }  // namespace mmk
+
+// Steps per launch of the persistent batch step.
+static constexpr int kBatchChunk = 1024;
 
 struct mm_batch {
     int ns = 0;
@@ -104,6 +168,13 @@ struct mm_batch {
     double exec_dt[2] = {0, 0};
     unsigned long long exec_ver[2] = {0, 0};
     unsigned long long ver = 1;
+    // persistent step: counters, co-resident grid, shared memory, choice
+    GridBar* gb = nullptr;
+    int pgrid = 0;
+    size_t psmem = 0;
+    int path = MM_STEP_AUTO;
+    long long wait_limit = kGridWaitLimit;
+    bool spec_valid = false;                   // S holds the x spectra of the current state
 };
 
 #define BCU(expr)                                                                                    \
@@ -171,6 +242,17 @@ static int batch_layout(mm_batch* b) {
     BCU(cudaFuncSetAttribute(k_batch_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[0]));
     BCU(cudaFuncSetAttribute(k_batch_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]));
     BCU(cudaFuncSetAttribute(k_batch_pass3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]));
+    {
+        size_t ps = sm[0] > sm[1] ? sm[0] : sm[1];
+        ps = ps > sm[2] ? ps : sm[2];
+        b->psmem = ps;
+        BCU(cudaFuncSetAttribute(k_batch_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps));
+        int dev = 0, sms = 0, per_sm = 0;
+        BCU(cudaGetDevice(&dev));
+        BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persist, b->threads, ps));
+        b->pgrid = per_sm * sms;
+    }
     BCU(cudaMemcpy(b->d_desc, b->desc.data(), sizeof(BatchDesc) * b->ns, cudaMemcpyHostToDevice));
     BCU(cudaMemcpy(b->d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     b->ver++;
@@ -200,6 +282,7 @@ static void batch_release(mm_batch* b) {
     cudaFree(b->d_desc);
     cudaFree(b->d_pre);
     cudaFree(b->flag);
+    cudaFree(b->gb);
     if (b->cap) cudaStreamDestroy(b->cap);
 }
 
@@ -276,6 +359,8 @@ extern "C" int mm_batch_create(mm_batch** out, int n, const int* grids, const do
         BCU(cudaMalloc(&b->d_pre, sizeof(int) * 3 * (n + 1)));
         BCU(cudaMalloc(&b->flag, sizeof(int)));
         BCU(cudaMemset(b->flag, 0, sizeof(int)));
+        BCU(cudaMalloc(&b->gb, sizeof(GridBar)));
+        BCU(cudaMemset(b->gb, 0, sizeof(GridBar)));
         std::vector<float2> htw(tt);
         std::vector<float> hm(mt);
         for (int s = 0; s < n; ++s) {
@@ -350,6 +435,7 @@ extern "C" int mm_batch_set_m(mm_batch* b, const float* M) {
     BCU(cudaMemcpyAsync(b->par ? b->M1 : b->M0, M, sizeof(float) * b->mtotal, cudaMemcpyDefault, b->stream));
     BCU(cudaMemsetAsync(b->flag, 0, sizeof(int), b->stream));
     BCU(cudaStreamSynchronize(b->stream));
+    b->spec_valid = false;
     return MM_OK;
 }
 
@@ -360,9 +446,56 @@ extern "C" int mm_batch_get_m(mm_batch* b, float* M) {
     return MM_OK;
 }
 
+// The persistent batch step is taken when asked for (MM_STEP_PERSISTENT)
+// and when every block of its grid fits on the device at once.
+static bool batch_uses_persist(const mm_batch* b) { return b->path == MM_STEP_PERSISTENT && b->pgrid > 0; }
+
+extern "C" int mm_batch_set_path(mm_batch* b, int path) {
+    if (!b) return set_error(MM_EINVAL, "null batch");
+    if (path != MM_STEP_AUTO && path != MM_STEP_GRAPH && path != MM_STEP_PERSISTENT)
+        return set_error(MM_EINVAL, "unknown step path");
+    if (path == MM_STEP_PERSISTENT && b->pgrid < 1)
+        return set_error(MM_EUNSUPPORTED, "the persistent batch step does not fit on this device");
+    b->path = path;
+    return MM_OK;
+}
+
+extern "C" int mm_batch_set_wait_limit(mm_batch* b, long long polls) {
+    if (!b) return set_error(MM_EINVAL, "null batch");
+    if (polls < 0) return set_error(MM_EINVAL, "polls must be >= 0");
+    b->wait_limit = polls;
+    return MM_OK;
+}
+
+static int batch_step_persist(mm_batch* b, int n, double dt) {
+    for (int s = 0; s < n;) {
+        const int m = n - s < kBatchChunk ? n - s : kBatchChunk;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(b->pgrid);
+        cfg.blockDim = dim3(b->threads);
+        cfg.dynamicSmemBytes = b->psmem;
+        cfg.stream = b->stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        BCU(cudaLaunchKernelEx(&cfg, k_batch_persist, (const BatchDesc*)b->d_desc, (const int*)b->d_pre, b->ns,
+                               b->tiles[0], b->tiles[1], b->tiles[2], b->par, m, (float)dt, b->spec_valid ? 0 : 1,
+                               b->flag, b->gb, b->wait_limit));
+        b->par = (b->par + m) & 1;
+        b->spec_valid = true;
+        s += m;
+    }
+    return MM_OK;
+}
+
 extern "C" int mm_batch_step(mm_batch* b, int n, double dt) {
     if (!b) return set_error(MM_EINVAL, "null batch");
     if (n < 0 || !(dt > 0.0) || !std::isfinite(dt)) return set_error(MM_EINVAL, "n >= 0 and dt > 0 required");
+    if (n == 0) return MM_OK;
+    if (batch_uses_persist(b)) return batch_step_persist(b, n, dt);
+    b->spec_valid = false;                     // the three-pass step leaves the plane output in S
     for (int s = 0; s < n; ++s) {
         const int p = b->par;
         if (!b->exec[p] || b->exec_dt[p] != dt || b->exec_ver[p] != b->ver) {
@@ -396,6 +529,7 @@ extern "C" int mm_batch_sync(mm_batch* b) {
     BCU(cudaStreamSynchronize(b->stream));
     int f = 0;
     BCU(cudaMemcpy(&f, b->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f & kFlagTimeout) return set_error(MM_ETIMEOUT, "a grid-barrier wait of the batch step gave up");
     if (f) return set_error(MM_ENONFINITE, "a batch step produced a non-finite magnetisation");
     return MM_OK;
 }
@@ -455,6 +589,7 @@ extern "C" int mm_batch_autotune(mm_batch* b, double dt, int choice[3], float* m
     cudaMemsetAsync(b->flag, 0, sizeof(int), b->stream);
     cudaStreamSynchronize(b->stream);
     cudaFree(save);
+    b->spec_valid = false;
     if (rc != MM_OK) return rc;
     if (choice) {
         choice[0] = b->r1;

@@ -145,33 +145,6 @@ template <int N> struct Fft2 {
         store_ex(v, t, ex);
     }
 
-    // Swizzled exchange without padding: element (a, t) sits at
-    // a Q + (t ^ sw(a)).  Step A stores a row at a time (one a, consecutive
-    // t across lanes) and step B loads a column at a time (one t, consecutive
-    // a across lanes); with the XOR both touch 16 distinct 8-byte bank pairs
-    // per half-warp, and the exchange fits in the N = P Q slots of the line
-    // itself, so a group can transpose in place with only warp barriers.
-    static __device__ __forceinline__ constexpr int sw(int a) { return Q >= 16 ? (a & 15) : ((a * Q / 16) % Q); }
-    static __device__ __forceinline__ void store_sw(const float2 (&v)[P], int t, float2* ex) {
-#pragma unroll
-        for (int a = 0; a < P; ++a) ex[a * Q + (t ^ sw(a))] = v[a];
-    }
-    static __device__ __forceinline__ void load_sw(float2 (&w)[Q], int a, const float2* ex) {
-        const int s = sw(a);
-#pragma unroll
-        for (int t = 0; t < Q; ++t) w[t] = ex[a * Q + (t ^ s)];
-    }
-    // Step A on registers with the table twiddles (no store).
-    static __device__ __forceinline__ void stepA_tab_reg(float2 (&v)[P], int t, const float2* ta, bool conj_in) {
-        if (conj_in) {
-#pragma unroll
-            for (int p = 0; p < P; ++p) v[p].y = -v[p].y;
-        }
-        dftp<P>(v);
-#pragma unroll
-        for (int a = 1; a < P; ++a) v[a] = cmul(v[a], ta[a * Q + t]);
-    }
-
     // Step B for thread a < P: gather ex[a][t], DFT_Q; w[b] = X[a + P b].
     static __device__ __forceinline__ void stepB(float2 (&w)[Q], int a, const float2* ex, bool conj_out) {
 #pragma unroll

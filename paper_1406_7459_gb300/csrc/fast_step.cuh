@@ -54,15 +54,17 @@ constexpr bool kEarlyTrigger = false;
 template <int NY, int NZ> struct PlaneLayout {
     using F = Fft2<NY>;
     static constexpr int LY = 2 * NY, NL = 3 * NZ;
-    static constexpr int ZS = 2 * NY + 2;                 // line stride: [h][m], two halves of NY
+    // a line is two halves [h] of F::EX slots: the first NY of a half hold
+    // its data in natural order, all F::EX serve as the padded exchange of
+    // that half's transform (Fft2::store_ex / stepB)
+    static constexpr int HALF = F::EX;
+    static constexpr int ZS = 2 * HALF;                   // line stride
     static constexpr int HY = NY + 1;
     static constexpr int HYP = kd_row(HY);                // row of the 2-D spectrum, 16-byte multiple
     static constexpr int KT_FLOATS = HYP * NZ * 6;        // one kx slice of the 2-D spectrum,
     // [dz*6 + c][ky] as stored, so that consecutive threads (consecutive ky)
     // read consecutive words
     static constexpr int KT_C = KT_FLOATS / 2;            // in float2 units
-    // the lines [line][h][m]; each half (NY slots) is also the swizzled
-    // exchange of its own transform (Fft2::store_sw / load_sw)
     static constexpr int WORK = NL * ZS;
     static constexpr int TW_OFF = 0, TA_OFF = LY, KT_OFF = LY + NY, WORK_OFF = KT_OFF + ((KT_C + 1) / 2) * 2;
     static constexpr size_t BYTES = sizeof(float2) * (WORK_OFF + WORK);
@@ -136,7 +138,7 @@ __device__ __forceinline__ void zdirect_task(const float2 (&m)[3][NZ], Coef coef
 // barrier b_k (phase 0).  2 NL groups of G threads, one per (line, half);
 // threads beyond them (T larger than the plane's own block) only help in
 // the z sum.  Each group transforms its half of a line in place in its own
-// NY slots of zb (warp barriers only); block barriers separate the forward
+// half of zb (warp barriers only); block barriers separate the forward
 // transforms, the z sum (which reads all lines of a column) and the inverse
 // transforms.  Returns false, uniformly over the block, when a copy wait gave
 // up (or ok_in is false); nothing is written to Sh then.
@@ -146,7 +148,7 @@ __device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, co
                                            float2* __restrict__ Sh) {
     using Lay = PlaneLayout<NY, NZ>;
     using F = Fft2<NY>;
-    constexpr int P = F::P, Q = F::Q, G = F::G, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
+    constexpr int P = F::P, Q = F::Q, G = F::G, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL, HALF = Lay::HALF;
     static_assert(T >= Lay::THREADS, "block smaller than the plane's groups");
     const unsigned lanes = warp_lanes<T>();
     const bool act = T == Lay::THREADS || threadIdx.x < Lay::THREADS;
@@ -173,18 +175,14 @@ __device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, co
     if (__syncthreads_or(!ok)) return false;
     // forward y (pruned input): odd half pre-multiplied by W_LY^j; the
     // group's own half-line is its exchange buffer
-    float2* rf = zb + lf * ZS + hf * NY;
+    float2* rf = zb + lf * ZS + hf * HALF;
     if (act && t < Q) {
         if (hf) F::odd_input_tab(v, t, tw);
-        F::stepA_tab_reg(v, t, ta, false);
-        F::store_sw(v, t, rf);
+        F::stepA_tab(v, t, ta, rf, false);
     }
     __syncwarp(lanes);
     float2 w[Q];
-    if (act && t < P) {
-        F::load_sw(w, t, rf);
-        dftp<Q>(w);
-    }
+    if (act && t < P) F::stepB(w, t, rf, false);
     __syncwarp(lanes);
     if (act && t < P) {
 #pragma unroll
@@ -197,7 +195,7 @@ __device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, co
     for (int col = threadIdx.x; col < LY; col += T) {
         const int hh = col / NY, mm = col - hh * NY;      // ky = 2 mm + hh
         const int ky = 2 * mm + hh;
-        const int e = hh * NY + mm;
+        const int e = hh * HALF + mm;
         float2 m[3][NZ];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -236,22 +234,16 @@ __device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, co
     }
     __syncthreads();
     // inverse y (pruned output), in place in the group's own half-line
-    float2* ri = zb + line * ZS + h * NY;
+    float2* ri = zb + line * ZS + h * HALF;
     if (act && t < Q) {
 #pragma unroll
         for (int q = 0; q < P; ++q) v[q] = ri[t + Q * q];
     }
     __syncwarp(lanes);
-    if (act && t < Q) {
-        F::stepA_tab_reg(v, t, ta, true);
-        F::store_sw(v, t, ri);
-    }
+    if (act && t < Q) F::stepA_tab(v, t, ta, ri, true);
     __syncwarp(lanes);
     if (act && t < P) {
-        F::load_sw(w, t, ri);
-        dftp<Q>(w);
-#pragma unroll
-        for (int b = 0; b < Q; ++b) w[b].y = -w[b].y;
+        F::stepB(w, t, ri, true);
         if (h) F::odd_output_tab(w, t, tw);
     }
     float2* outp = Sh + (size_t)kx * NL * g.Jst;
@@ -274,7 +266,7 @@ __device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, co
 #pragma unroll
         for (int idx = threadIdx.x; idx < NL * NY; idx += T) {
             const int l = idx / NY, n = idx % NY;
-            outp[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + NY + n]);
+            outp[(size_t)l * g.Jst + n] = cadd(zb[l * ZS + n], zb[l * ZS + HALF + n]);
         }
     }
     return true;

@@ -22,64 +22,9 @@
 // launch must make every block co-resident (cooperative launch attribute).
 #pragma once
 #include "fast_step.cuh"
+#include "grid_sync.cuh"
 
 namespace mmk {
-
-// Counters of the grid barrier (one per context, zeroed at creation).
-struct GridBar {
-    unsigned count;        // arrivals in this launch (every block once per barrier)
-    unsigned exits;        // blocks that have left the launch
-    unsigned pad[2];
-};
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Barrier number `k` (0, 1, 2, ... within the launch): every block of the
-// grid arrives before any proceeds; the writes of every thread before it are
-// visible to every thread after it.  Each block adds 1 to the launch's
-// arrival count and waits for it to reach (k + 1) blocks; the waits poll
-// with a short sleep so that the arrivals are not slowed by the polls.
-// Returns false, uniformly over the block, when its wait ran out of polls
-// (limit 0: gives up at once unless every block has already arrived).
-__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned k, long long limit) {
-    __syncthreads();
-    int ok = 1;
-    if (threadIdx.x == 0) {
-        const unsigned target = (k + 1) * gridDim.x;
-        __threadfence();
-        red_release_add(&gb->count, 1u);
-        long long it = 0;
-        while ((int)(ld_acquire_gpu(&gb->count) - target) < 0) {
-            if (it++ >= limit) {
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-    }
-    return __syncthreads_and(ok) != 0;
-}
-
-// Last act of every block: the last one out clears the counters for the
-// next launch.
-__device__ __forceinline__ void grid_exit(GridBar* gb) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&gb->exits, 1u) == gridDim.x - 1) {
-            atomicExch(&gb->count, 0u);
-            atomicExch(&gb->exits, 0u);
-        }
-    }
-}
 
 // Shared memory of the persistent step (float2 units; every region starts
 // on 16 bytes).  Resident: y twiddles and their table, the plane's 2-D

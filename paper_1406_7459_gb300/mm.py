@@ -67,6 +67,8 @@ _PROTOS = {
     "mm_batch_set_m": (_c_int, [_vp, _vp]),
     "mm_batch_get_m": (_c_int, [_vp, _vp]),
     "mm_batch_step": (_c_int, [_vp, _c_int, _c_double]),
+    "mm_batch_set_path": (_c_int, [_vp, _c_int]),
+    "mm_batch_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
     "mm_batch_sync": (_c_int, [_vp]),
     "mm_batch_cells": (ctypes.c_longlong, [_vp]),
     "mm_batch_autotune": (_c_int, [_vp, _c_double, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float)]),
@@ -342,6 +344,14 @@ def mm_batch_step(b, n, dt):
 
 def mm_batch_sync(b):
     _check(lib().mm_batch_sync(b.handle))
+
+
+def mm_batch_set_path(b, path):
+    _check(lib().mm_batch_set_path(b.handle, int(path)))
+
+
+def mm_batch_set_wait_limit(b, polls):
+    _check(lib().mm_batch_set_wait_limit(b.handle, int(polls)))
 
 
 def mm_batch_cells(b):

@@ -69,3 +69,22 @@ def test_recorded_traffic_only_for_the_captured_kernel_sources(tmp_path):
     assert bench.recorded_traffic("kA_plane_y_zsum_product", str(f)) is None
     f.write_text(json.dumps({"kA_plane_y_zsum_product": 1.5e7}))
     assert bench.recorded_traffic("kA_plane_y_zsum_product", str(f)) is None
+
+
+def test_batch_byte_model_uses_the_plan_lengths():
+    """bench.batch_bytes: the three-pass and fused byte models summed over
+    samples, with the padded lengths of the plan (restated in the tests'
+    helpers independently)."""
+    from tests._helpers import padded_length
+    for n in list(range(1, 300)) + [512, 1000, 2048]:
+        assert bench.padded_length(n) == padded_length(n), n
+    grids = [(256, 256, 4), (200, 60, 3), (17, 33, 1)]
+    by = bench.batch_bytes(grids)
+    g3 = sum(bench.algorithmic_bytes(g)["step3"] for g in grids[:1])
+    assert by["graph"] > g3 and by["persistent"] < by["graph"]
+    nx, ny, nz = 200, 60, 3
+    X = (400 // 2 + 1) * ny * nz
+    Ks = (400 // 2 + 1) * (120 // 2 + 1) * (5 // 2 + 1)          # Lz = 5 for nz = 3
+    one = bench.batch_bytes([(nx, ny, nz)])
+    assert one["graph"] == 36 * nx * ny * nz + 96 * X + 24 * Ks
+    assert one["graph"] - one["persistent"] == 12 * nx * ny * nz

@@ -116,3 +116,66 @@ def test_full_batch_workload_sampled(monkeypatch):
         mm.mm_get_m(ctx, one)
         mm.mm_sync(ctx)
         assert np.array_equal(one.cpu().numpy(), mine), (i, g, choice)
+
+
+def _run_path(samples, path, runs, dt=5e-14, autotune=False):
+    from paper_1406_7459_gb300 import mm
+    b = _make(samples)
+    if autotune:
+        mm.mm_batch_autotune(b, dt)
+    mm.mm_batch_set_path(b, path)
+    for n in runs:
+        mm.mm_batch_step(b, n, dt)
+    out = torch.empty(b.total, device="cuda")
+    mm.mm_batch_get_m(b, out)
+    mm.mm_batch_sync(b)
+    return out.cpu().numpy()
+
+
+def test_persistent_batch_is_bitwise_the_graph_batch():
+    """One cooperative launch per call, (sample, tile) items taken from a
+    work queue per pass, against the three batched kernels per step of the
+    graph path: runs of 1, 3 and 6 steps (the spectra carried from one call to
+    the next) give the same bits."""
+    from paper_1406_7459_gb300 import mm
+    samples = inputs.batch_samples(10, seed=7, nx=(16, 96), ny=(16, 40), nz=(1, 3))
+    a = _run_path(samples, mm.MM_STEP_PERSISTENT, (1, 3, 6))
+    b = _run_path(samples, mm.MM_STEP_GRAPH, (1, 3, 6))
+    assert np.all(np.isfinite(a))
+    assert np.array_equal(a, b)
+
+
+def test_persistent_full_batch_workload_is_bitwise_the_graph_batch():
+    """The benchmarked 512-sample batch, autotuned, four steps both ways."""
+    from paper_1406_7459_gb300 import mm
+    samples = inputs.batch_samples(512, seed=3)
+    a = _run_path(samples, mm.MM_STEP_PERSISTENT, (4,), autotune=True)
+    b = _run_path(samples, mm.MM_STEP_GRAPH, (4,), autotune=True)
+    assert np.array_equal(a, b)
+
+
+def test_persistent_batch_wait_gives_up_and_recovers():
+    """A poll limit of 0: the grid-barrier waits give up at once and
+    mm_batch_sync reports MM_ETIMEOUT (no GPU fault).  After the limit is
+    restored and the state set again, the batch steps as the graph path."""
+    from paper_1406_7459_gb300 import mm
+    samples = inputs.batch_samples(10, seed=8, nx=(16, 96), ny=(16, 40), nz=(1, 2))
+    b = _make(samples)
+    mm.mm_batch_set_path(b, mm.MM_STEP_PERSISTENT)
+    mm.mm_batch_set_wait_limit(b, 0)
+    mm.mm_batch_step(b, 3, 5e-14)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_batch_sync(b)
+    assert e.value.code == mm.MM_ETIMEOUT
+    mm.mm_batch_set_wait_limit(b, 1 << 20)
+    M = np.concatenate([s["M"].reshape(-1) for s in samples])
+    mm.mm_batch_set_m(b, torch.from_numpy(M).cuda())
+    mm.mm_batch_step(b, 3, 5e-14)
+    out = torch.empty(b.total, device="cuda")
+    mm.mm_batch_get_m(b, out)
+    mm.mm_batch_sync(b)
+    ref = _run_path(samples, mm.MM_STEP_GRAPH, (3,))
+    assert np.array_equal(out.cpu().numpy(), ref)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_batch_set_path(b, 9)
+    assert e.value.code == mm.MM_EINVAL
