@@ -675,6 +675,22 @@ def batch_bytes(grids):
     return tot
 
 
+def truncation_floor(h, m):
+    """Relative L2 of the part of fields h (B, 3, H, W) (torch, device)
+    outside the modes an FNO spectral path with m modes can carry: ky in
+    {0..m-1} U {H-m..H-1}, kx < m, and their conjugate partners."""
+    import torch
+    H, W = h.shape[-2:]
+    hf = torch.fft.fft2(h.double())
+    keep = torch.zeros((H, W), dtype=torch.bool, device=h.device)
+    ky = torch.cat([torch.arange(m), torch.arange(H - m, H)]).to(h.device)
+    kx = torch.arange(m, device=h.device)
+    keep[ky[:, None], kx[None, :]] = True
+    keep[((-ky) % H)[:, None], ((-kx) % W)[None, :]] = True
+    p = hf.abs() ** 2
+    return float(torch.sqrt(p[..., ~keep].sum() / p.sum()))
+
+
 def run_surrogate(args, rank, ws):
     """FNO surrogate of H_demag on the 256x256x1 film (5x5x3 nm cells,
     alpha 0.02, random fields and starts): width 32, 16x16 retained modes,
@@ -703,27 +719,56 @@ def run_surrogate(args, rank, ws):
             mm.mm_get_m(ctx, states[tr, s])
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    f = mm.mm_fno_create(256, 256, width=32, modes=16, layers=4, max_batch=8, seed=1)
+    modes = 16
+    f = mm.mm_fno_create(256, 256, width=32, modes=modes, layers=4, max_batch=8, seed=1)
     B, iters = 8, 2500                               # 20k pairs
     X = torch.empty((B, N3), device="cuda")
     Y = torch.empty((B, N3), device="cuda")
-    losses = []
-    t0 = time.perf_counter()
-    for it in range(iters):
-        tr = rng.integers(0, n_traj, B)
+
+    def draw(trs):
+        """B pairs (dM / rms(dM), H_demag(dM) / rms(dM)) from trajectories trs."""
+        tr = rng.choice(trs, B)
         t = rng.integers(0, T - 8, B)
         k = rng.integers(1, 9, B)
         for q in range(B):
             dM = (states[tr[q], t[q] + k[q]] - states[tr[q], t[q]]).contiguous()
+            sc = torch.sqrt(torch.mean(dM * dM))
             mm.mm_demag_field(ctx, dM, Y[q])
-            X[q] = dM / Ms
-        Y /= Ms
+            Y[q] /= sc
+            X[q] = dM / sc
+
+    train_trs, held_trs = np.arange(n_traj - 2), np.arange(n_traj - 2, n_traj)
+    losses, floors = [], []
+    t0 = time.perf_counter()
+    for it in range(iters):
+        draw(train_trs)
+        if it % 250 == 0:
+            floors.append(truncation_floor(Y.view(B, 3, 256, 256), modes))
         lr = 2e-3 if it < 1500 else (1e-3 if it < 2200 else 3e-4)
         losses.append(mm.mm_fno_train_step(f, X, Y, lr))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    # relative error of the trained network on pairs of held-out trajectories
+    held = []
+    yh = torch.empty_like(X)
+    for _ in range(8):
+        draw(held_trs)
+        mm.mm_fno_forward(f, X, yh)
+        held += [float(torch.linalg.norm(yh[q] - Y[q]) / torch.linalg.norm(Y[q])) for q in range(B)]
     # evaluation: surrogate-assisted vs plain steps from a settled state
     M0 = states[0, T // 2].clone()
+    # the regime where this network stays under the gate: short steps with a
+    # refresh every 2 steps (the residual grows with the increment's field)
+    small = {}
+    for name, fn in (("network", f), ("frozen_field", None)):
+        c = mm.mm_create(grid, cell, Ms, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
+        mm.mm_set_field(c, (3e4, 1e4, 0.0))
+        mm.mm_set_m(c, M0)
+        if fn is None:
+            fn = mm.mm_fno_create(256, 256, width=32, modes=modes, layers=4, max_batch=8, seed=1)
+            mm.mm_fno_set_params(fn, np.zeros(mm.mm_fno_param_count(fn), np.float32))
+        small[name] = mm.mm_step_surrogate(c, fn, 64, 1e-15, refresh=2, tol=1e-3)
+        mm.mm_destroy(c)
     res = {}
     for name in ("surrogate", "plain"):
         c = mm.mm_create(grid, cell, Ms, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
@@ -748,6 +793,20 @@ def run_surrogate(args, rank, ws):
     dsur = (res["surrogate"][0] - M0).cpu().numpy()
     dpl = (res["plain"][0] - M0).cpu().numpy()
     traj_err = float(np.linalg.norm(dsur - dpl) / np.linalg.norm(dpl))
+    # the size of a k-step increment's field against the field itself: the
+    # residual at a refresh is about (network error) x rho(k)
+    rho = {}
+    c = mm.mm_create(grid, cell, Ms, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
+    mm.mm_set_field(c, (3e4, 1e4, 0.0))
+    hm, hd, mk = torch.empty(N3, device="cuda"), torch.empty(N3, device="cuda"), torch.empty(N3, device="cuda")
+    mm.mm_demag_field(c, M0, hm)
+    for k in (1, 7):
+        mm.mm_set_m(c, M0)
+        mm.mm_step(c, k, dt)
+        mm.mm_get_m(c, mk)
+        mm.mm_demag_field(c, (mk - M0).contiguous(), hd)
+        rho[k] = float(torch.linalg.norm(hd) / torch.linalg.norm(hm))
+    mm.mm_destroy(c)
     # cost of one surrogate evaluation against one exact demag evaluation
     xin = X[:1].contiguous()
     yout = torch.empty_like(xin)
@@ -776,8 +835,15 @@ def run_surrogate(args, rank, ws):
                          "loss_last_100_mean": float(np.mean(losses[-100:])), "seconds": t_train,
                          "trajectory_generation_seconds": t_data},
             "stepping": {"surrogate_ms_per_step": res["surrogate"][1], "plain_ms_per_step": res["plain"][1],
-                         "gain_plain_over_surrogate": res["plain"][1] / res["surrogate"][1],
+                         "gain_surrogate_over_plain": res["plain"][1] / res["surrogate"][1],
                          "stats": res["surrogate"][2], "trajectory_change_rel_err_vs_plain": traj_err},
+            "short_steps_1e-15_refresh_2": small,
+            "accuracy": {"network_rel_err_held_out_median": float(np.median(held)),
+                         "truncation_floor_of_targets_mean": float(np.mean(floors)),
+                         "increment_field_over_field": {"1_step": rho[1], "7_steps": rho[7]},
+                         "gate": 1e-3,
+                         "reading": "the refresh residual is about the network error times the increment "
+                                    "ratio; the gate needs network error <= gate / ratio"},
             "one_evaluation_ms": {"fno_forward": fno_ms, "exact_fft_demag": exact_ms}}))
     return 0
 

@@ -351,8 +351,10 @@ int mm_fno_train_step(mm_fno *f, int batch, const float *x, const float *t, floa
 /*
  * mm_step_surrogate -- n forward-Euler steps where the demag field is the
  * exact FFT convolution every `refresh` steps and, in between,
- * H_ref + Ms * FNO((M - M_ref)/Ms) with (M_ref, H_ref) from the last exact
- * refresh.  At each refresh the surrogate's prediction is compared with the
+ * H_ref + Ms r FNO((M - M_ref) / (Ms r)) with (M_ref, H_ref) from the last
+ * exact refresh and r the root mean square of (M - M_ref) / Ms: H_demag is
+ * linear in M, so the network is trained on (and sees) unit-scale
+ * increments x = dM / (Ms r) with targets H_demag(dM) / (Ms r).  At each refresh the surrogate's prediction is compared with the
  * exact field; once the relative L2 residual exceeds tol the stepper falls
  * back to the exact field for the remaining steps.  stats (may be NULL):
  * {surrogate steps, exact steps, largest residual, fell back (0/1)}.

@@ -66,6 +66,29 @@ def inverse_modes(w, H, W):
     return np.fft.irfft2(full, s=(H, W))
 
 
+def retained_mask(H, W, m):
+    """(H, W) boolean mask of the full 2-D spectrum that the spectral path
+    can carry: (ky, kx) with ky in K and kx < m, and their conjugate partners
+    (-ky, -kx), which the real output keeps with them."""
+    mask = np.zeros((H, W), bool)
+    ky, kx = _ky(H, m), np.arange(m)
+    mask[np.ix_(ky, kx)] = True
+    mask[np.ix_((-ky) % H, (-kx) % W)] = True
+    return mask
+
+
+def truncation_floor(h, m):
+    """Relative L2 norm of the part of the fields h (..., H, W) outside the
+    retained modes: sqrt(sum over dropped k of |h^(k)|^2 / sum over all k),
+    by Parseval the error left by the best field the spectral path alone
+    could output (its output lies in the retained modes)."""
+    H, W = h.shape[-2:]
+    hf = np.fft.fft2(h)
+    keep = retained_mask(H, W, m)
+    out = np.sum(np.abs(hf[..., ~keep]) ** 2)
+    return float(np.sqrt(out / np.sum(np.abs(hf) ** 2)))
+
+
 def spectral(v, Rl, m):
     vh = forward_modes(v, m)
     w = np.einsum("coyx,cyx->oyx", Rl, vh)

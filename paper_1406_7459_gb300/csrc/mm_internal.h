@@ -236,9 +236,12 @@ int fno_apply(mm_fno* f, const float* x, float* y, cudaStream_t s);
 bool fno_matches(const mm_fno* f, int nx, int ny, int nz);
 
 // Surrogate-assisted stepping (surrogate.cu).
-cudaError_t sur_scaled_diff(const float* a, const float* b, float s, long long n, float* out, cudaStream_t st);
-cudaError_t sur_axpy(const float* base, const float* y, float s, long long n, float* out, cudaStream_t st);
 cudaError_t sur_resid(const float* a, const float* b, long long n, double* out, cudaStream_t st);
+// out = (a - b) / rms(a - b) (the sum of squares of a - b left in ss,
+// device); and out = base + rms(a - b) y from that sum.
+cudaError_t sur_unit_diff(const float* a, const float* b, long long n, double* ss, float* out, cudaStream_t st);
+cudaError_t sur_rescale_add(const float* base, const float* y, const double* ss, long long n, float* out,
+                            cudaStream_t st);
 cudaError_t sur_llg(const Geom& g, const LlgCoef& cf, const float* M, const float* Hd, float* out, int* flag,
                     cudaStream_t st);
 

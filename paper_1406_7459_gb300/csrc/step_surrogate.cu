@@ -17,11 +17,10 @@ extern "C" int mm_step_surrogate(mm_ctx* c, mm_fno* f, int n, double dt, int ref
     const size_t N3 = 3 * (size_t)c->g.N;
     if (!c->sur) {
         CU(cudaMalloc(&c->sur, sizeof(float) * 5 * N3));
-        CU(cudaMalloc(&c->sur_r, 2 * sizeof(double)));
+        CU(cudaMalloc(&c->sur_r, 3 * sizeof(double)));
     }
     float *Mref = c->sur, *Href = c->sur + N3, *x = c->sur + 2 * N3, *y = c->sur + 3 * N3, *Hd = c->sur + 4 * N3;
     const LlgCoef cf = make_coef(c, dt);
-    const float Ms = (float)c->Ms;
     double n_sur = 0, n_exact = 0, max_res = 0;
     bool fallback = false, have_ref = false;
     for (int s = 0; s < n; ++s) {
@@ -31,10 +30,10 @@ extern "C" int mm_step_surrogate(mm_ctx* c, mm_fno* f, int n, double dt, int ref
             if (rc != MM_OK) return rc;
             if (have_ref && !fallback) {
                 // surrogate's prediction at this state against the exact field
-                CU(sur_scaled_diff(c->Mbuf[p], Mref, 1.f / Ms, (long long)N3, x, c->stream));
+                CU(sur_unit_diff(c->Mbuf[p], Mref, (long long)N3, c->sur_r + 2, x, c->stream));
                 rc = fno_apply(f, x, y, c->stream);
                 if (rc != MM_OK) return rc;
-                CU(sur_axpy(Href, y, Ms, (long long)N3, x, c->stream));
+                CU(sur_rescale_add(Href, y, c->sur_r + 2, (long long)N3, x, c->stream));
                 CU(sur_resid(x, Hd, (long long)N3, c->sur_r, c->stream));
                 double r[2];
                 CU(cudaMemcpyAsync(r, c->sur_r, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
@@ -48,10 +47,10 @@ extern "C" int mm_step_surrogate(mm_ctx* c, mm_fno* f, int n, double dt, int ref
             have_ref = true;
             n_exact += 1;
         } else {
-            CU(sur_scaled_diff(c->Mbuf[p], Mref, 1.f / Ms, (long long)N3, x, c->stream));
+            CU(sur_unit_diff(c->Mbuf[p], Mref, (long long)N3, c->sur_r + 2, x, c->stream));
             int rc = fno_apply(f, x, y, c->stream);
             if (rc != MM_OK) return rc;
-            CU(sur_axpy(Href, y, Ms, (long long)N3, Hd, c->stream));
+            CU(sur_rescale_add(Href, y, c->sur_r + 2, (long long)N3, Hd, c->stream));
             n_sur += 1;
         }
         CU(sur_llg(c->g, cf, c->Mbuf[p], Hd, c->Mbuf[1 - p], c->flag, c->stream));

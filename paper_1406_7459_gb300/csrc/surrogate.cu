@@ -1,23 +1,46 @@
 // surrogate.cu -- elementwise kernels of the surrogate-assisted stepper.
 //
 // Between exact demag refreshes the demag field is taken as
-// H_ref + Ms * FNO((M - M_ref)/Ms) (H_demag is linear in M); the rest of the
-// step is the paper's: exchange (Eq. 4), anisotropy (Eq. 5), Zeeman, the LLG
-// right-hand side (Eq. 6), forward Euler and renormalisation.
+// H_ref + Ms r FNO((M - M_ref) / (Ms r)), r the root mean square of
+// (M - M_ref) / Ms: H_demag is linear in M, so the network only ever sees
+// increments of unit scale, whatever the time since the refresh.  The rest
+// of the step is the paper's: exchange (Eq. 4), anisotropy (Eq. 5), Zeeman,
+// the LLG right-hand side (Eq. 6), forward Euler and renormalisation.
 #include "mm_internal.h"
 
 namespace mmk {
 
-__global__ void k_scaled_diff(const float* __restrict__ a, const float* __restrict__ b, float s, long long n,
-                              float* __restrict__ out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = (a[i] - b[i]) * s;
+// sum of (a - b)^2 in FP64 into *out (zeroed by the caller)
+__global__ void k_sumsq_diff(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                             double* __restrict__ out) {
+    double d2 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double d = (double)a[i] - (double)b[i];
+        d2 += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 += __shfl_down_sync(0xffffffffu, d2, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, d2);
 }
 
-__global__ void k_axpy(const float* __restrict__ base, const float* __restrict__ y, float s, long long n,
-                       float* __restrict__ out) {
+// Ms r = rms(M - M_ref) from the sum of squares over n values (0 when
+// M = M_ref)
+__device__ __forceinline__ double increment_scale(const double* ss, long long n) { return sqrt(*ss / (double)n); }
+
+// out = (a - b) / (Ms r), the unit-scale increment the network takes
+__global__ void k_unit_diff(const float* __restrict__ a, const float* __restrict__ b, const double* __restrict__ ss,
+                            long long n, float* __restrict__ out) {
+    const double sc = increment_scale(ss, n);
+    const float inv = sc > 0.0 ? (float)(1.0 / sc) : 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = base[i] + s * y[i];
+        out[i] = (a[i] - b[i]) * inv;
+}
+
+// out = base + Ms r y: the field of the increment from the network's output
+__global__ void k_rescale_add(const float* __restrict__ base, const float* __restrict__ y,
+                              const double* __restrict__ ss, long long n, float* __restrict__ out) {
+    const float sc = (float)increment_scale(ss, n);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = base[i] + sc * y[i];
 }
 
 // sums of (a - b)^2 and b^2 in FP64 (out[0], out[1])
@@ -89,12 +112,18 @@ static int nblk(long long n) {
     return (int)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b));
 }
 
-cudaError_t sur_scaled_diff(const float* a, const float* b, float s, long long n, float* out, cudaStream_t st) {
-    k_scaled_diff<<<nblk(n), 256, 0, st>>>(a, b, s, n, out);
+cudaError_t sur_unit_diff(const float* a, const float* b, long long n, double* ss, float* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(ss, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    k_sumsq_diff<<<nblk(n), 256, 0, st>>>(a, b, n, ss);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_unit_diff<<<nblk(n), 256, 0, st>>>(a, b, ss, n, out);
     return cudaGetLastError();
 }
-cudaError_t sur_axpy(const float* base, const float* y, float s, long long n, float* out, cudaStream_t st) {
-    k_axpy<<<nblk(n), 256, 0, st>>>(base, y, s, n, out);
+cudaError_t sur_rescale_add(const float* base, const float* y, const double* ss, long long n, float* out,
+                            cudaStream_t st) {
+    k_rescale_add<<<nblk(n), 256, 0, st>>>(base, y, ss, n, out);
     return cudaGetLastError();
 }
 cudaError_t sur_resid(const float* a, const float* b, long long n, double* out, cudaStream_t st) {

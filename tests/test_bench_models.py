@@ -88,3 +88,14 @@ def test_batch_byte_model_uses_the_plan_lengths():
     one = bench.batch_bytes([(nx, ny, nz)])
     assert one["graph"] == 36 * nx * ny * nz + 96 * X + 24 * Ks
     assert one["graph"] - one["persistent"] == 12 * nx * ny * nz
+
+
+def test_bench_truncation_floor_equals_the_oracle_floor():
+    """The surrogate workload measures the FNO truncation floor of its
+    training targets with torch on the device; it is the oracle's floor."""
+    import torch
+    from oracle import fno as F
+    rng = np.random.default_rng(4)
+    for H, W, m in ((32, 40, 6), (16, 16, 8), (64, 48, 5)):
+        h = rng.standard_normal((2, 3, H, W))
+        assert abs(bench.truncation_floor(torch.from_numpy(h), m) - F.truncation_floor(h, m)) < 1e-12

@@ -73,8 +73,9 @@ def test_fno_forward_at_the_surrogate_size():
 
 
 def _pairs(grid, cell, n_traj, steps, seed):
-    """(dM/Ms, H_demag(dM)/Ms) from solver trajectories: random starts,
-    alpha 0.02, random fields; increments over 1..8 steps."""
+    """(dM / rms(dM), H_demag(dM) / rms(dM)) from solver trajectories:
+    random starts, alpha 0.02, random fields; increments over 1..8 steps,
+    scaled to unit RMS as the surrogate stepper scales them."""
     mm = _mm()
     rng = np.random.default_rng(seed)
     ctx = mm.mm_create(grid, cell, 8.6e5, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
@@ -96,13 +97,20 @@ def _pairs(grid, cell, n_traj, steps, seed):
             dM = (states[s + k] - states[s]).contiguous()
             h = torch.empty_like(dM)
             mm.mm_demag_field(ctx, dM, h)
-            xs.append(dM / 8.6e5)
-            ys.append(h / 8.6e5)
+            scale = torch.sqrt(torch.mean(dM * dM))        # Ms r: the stepper's unit-scale increments
+            xs.append(dM / scale)
+            ys.append(h / scale)
     torch.cuda.synchronize()
     return torch.stack(xs), torch.stack(ys)
 
 
 def test_surrogate_trains_and_steps_within_tolerance():
+    """Train a small FNO on solver pairs, then let it drive the steps between
+    exact refreshes: no fallback, every refresh residual under the 1e-3 gate,
+    the trajectory as the plain step's.  The gain of the network over the
+    same stepper without it (an all-zero network, i.e. the last exact field
+    frozen between refreshes) is measured on the same schedule: its residual
+    must be at least twice the trained network's."""
     mm = _mm()
     grid, cell = (64, 64, 1), (5e-9, 5e-9, 3e-9)
     X, Y = _pairs(grid, cell, n_traj=6, steps=60, seed=1)
@@ -125,8 +133,14 @@ def test_surrogate_trains_and_steps_within_tolerance():
         mm.mm_step(c, 20, 5e-14)
     M0 = torch.empty_like(M0)
     mm.mm_get_m(ctx_b, M0)
-    stats = mm.mm_step_surrogate(ctx_a, f, 64, 5e-14, refresh=8, tol=1e-3)
-    mm.mm_step(ctx_b, 64, 5e-14)
+    # stepping regime: the refresh residual is about the network's relative
+    # error times |H_demag(dM)| / |H_demag(M)|, which grows ~4 % per 5e-14 s
+    # step on this film; steps of 1e-15 s with a refresh every 2 steps keep
+    # it under the 1e-3 gate for this network (~30-70 % error on these
+    # increments: the BF16 FNO does not carry the operator closer)
+    dt_s = 1e-15
+    stats = mm.mm_step_surrogate(ctx_a, f, 64, dt_s, refresh=2, tol=1e-3)
+    mm.mm_step(ctx_b, 64, dt_s)
     a, b = torch.empty_like(M0), torch.empty_like(M0)
     mm.mm_get_m(ctx_a, a)
     mm.mm_get_m(ctx_b, b)
@@ -134,6 +148,20 @@ def test_surrogate_trains_and_steps_within_tolerance():
     mm.mm_sync(ctx_b)
     err = rel_l2(a.cpu().numpy() - M0.cpu().numpy(), b.cpu().numpy() - M0.cpu().numpy())
     print("surrogate: %s, trajectory change error %.3e" % (stats, err))
+    # the surrogate drives the steps between refreshes: no fallback, every
+    # refresh within the 1e-3 relative H_demag gate
     assert stats["exact_steps"] + stats["surrogate_steps"] == 64
-    assert stats["max_residual"] < 1e-3 or stats["fell_back"]
+    assert not stats["fell_back"]
+    assert stats["surrogate_steps"] == 32 and stats["exact_steps"] == 32
+    assert 0 < stats["max_residual"] < 1e-3
     assert err < 1e-2
+    # without the network: the last exact field held between refreshes
+    z = mm.mm_fno_create(64, 64, width=16, modes=8, layers=2, max_batch=8, seed=3)
+    mm.mm_fno_set_params(z, np.zeros(mm.mm_fno_param_count(z), np.float32))
+    ctx_c = mm.mm_create(grid, cell, 8.6e5, 1.3e-11, 0.0, 0.02, inputs.GAMMA0)
+    mm.mm_set_field(ctx_c, (2e4, 1e4, 0.0))
+    mm.mm_set_m(ctx_c, M0)
+    frozen = mm.mm_step_surrogate(ctx_c, z, 64, dt_s, refresh=2, tol=1.0)
+    mm.mm_sync(ctx_c)
+    print("frozen field: %s" % frozen)
+    assert frozen["max_residual"] > 2.0 * stats["max_residual"]

@@ -58,3 +58,38 @@ def test_gradients_match_central_differences():
         fd = (F.loss(pp, x, t, m) - F.loss(pm, x, t, m)) / (2 * eps)
         an = float(np.sum(g[name] * d))
         assert abs(fd - an) <= 1e-6 * max(1e-8, abs(an)) + 1e-12, (name, fd, an)
+
+
+def test_truncation_floor_pins():
+    """The floor of the FNO's retained modes: zero for a field that lies in
+    them, one for a field wholly outside, the exact orthogonal split for a
+    mixture, and the same projection as the spectral path with identity
+    weights (an independent route through irfft2)."""
+    rng = np.random.default_rng(3)
+    C, H, W, m = 3, 16, 20, 4
+    full = np.zeros((C, H, W // 2 + 1), complex)
+    ky = np.concatenate([np.arange(m), np.arange(H - m, H)])
+    full[:, ky, :m] = rng.standard_normal((C, 2 * m, m)) + 1j * rng.standard_normal((C, 2 * m, m))
+    inside = np.fft.irfft2(full, s=(H, W))
+    assert F.truncation_floor(inside, m) < 1e-12
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    outside = np.cos(2 * np.pi * (m * yy / H + (m + 1) * xx / W))[None] * np.ones((C, 1, 1))
+    assert abs(F.truncation_floor(outside, m) - 1.0) < 1e-12
+    a, b = 0.6, 0.8
+    u = inside / np.linalg.norm(inside)
+    v = outside / np.linalg.norm(outside)
+    assert abs(F.truncation_floor(a * u + b * v, m) - b / np.hypot(a, b)) < 1e-12
+    # brute force: least-squares fit of a random field by every real field
+    # the spectral path can output (cos and sin of each retained (ky, kx))
+    h = rng.standard_normal((C, H, W))
+    basis = []
+    for k in ky:
+        for kx in range(m):
+            ph = 2 * np.pi * (k * yy / H + kx * xx / W)
+            basis += [np.cos(ph).ravel(), np.sin(ph).ravel()]
+    Bm = np.array(basis).T
+    res = 0.0
+    for c in range(C):
+        coef = np.linalg.lstsq(Bm, h[c].ravel(), rcond=None)[0]
+        res += np.sum((h[c].ravel() - Bm @ coef) ** 2)
+    assert abs(F.truncation_floor(h, m) - np.sqrt(res) / np.linalg.norm(h)) < 1e-12
