@@ -146,7 +146,10 @@ int mm_set_field(mm_ctx *ctx, const double H_ext[3]);
 
 /* mm_set_m -- copy a magnetisation state into the context (Sec. 3: the
  * initial conditions are the only host-to-device input).  M: 3*N float32,
- * host or device.  Used as given: the caller supplies |M| = Ms. */
+ * host or device.  Used as given, not renormalised: the caller supplies
+ * |M| = Ms (a departure from a set-and-renormalise contract, so that a state
+ * read with mm_get_m and set again is bit for bit the same state; every
+ * step renormalises its result to Ms). */
 int mm_set_m(mm_ctx *ctx, const float *M);
 
 /* mm_get_m -- copy the current magnetisation out.  M: 3*N float32, host or

@@ -1,7 +1,6 @@
 """Precision study on the large grids: FP32 GPU path against the FP64
 oracle.  Long (minutes of oracle time), so it runs only with
-MM_PRECISION_STUDY=1; the numbers it prints are the ones the design notes
-quote.
+MM_PRECISION_STUDY=1; it prints the error of each result as a number.
 
 Film 1024x1024x1 and block 256x256x64, 2.5 nm cells, Ms 8.6e5, A 1.3e-11,
 Ku 0, alpha 0.5, smooth start (+x with a seed-2 perturbation of 0.1,
