@@ -312,6 +312,9 @@ def run_gpu(args, rank, ws):
     w = workload()
     N = GRID[0] * GRID[1] * GRID[2]
     ctx = mm.mm_create(GRID, w["cell"], w["Ms"], w["A"], w["Ku"], w["alpha"], w["gamma"])
+    mm.mm_set_step_path(ctx, {"auto": mm.MM_STEP_AUTO, "graph": mm.MM_STEP_GRAPH,
+                              "persistent": mm.MM_STEP_PERSISTENT}[args.step_path])
+    step_path = "persistent" if mm.mm_get_step_path(ctx) == mm.MM_STEP_PERSISTENT else "graph"
     mm.mm_set_field(ctx, w["H_ext"])
     M0 = inputs.uniform_m(GRID, w["Ms"], w["start"]).reshape(-1)
     mm.mm_set_m(ctx, torch.from_numpy(M0).cuda())
@@ -432,12 +435,13 @@ def run_gpu(args, rank, ws):
                              "frac_at_step_time": None},
         "alu": alu,
         "pass_ms": passes,
-        "launches_per_step": launches,
+        "launches_per_step": launches if step_path == "graph" else "one launch per mm_step call",
+        "step_path": step_path,
         "steady_state_l2_resident": {"ms_per_step": warm_ms, "cells_steps_per_s": ws * N / (warm_ms * 1e-3)},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": kbytes[dom]},
-        "gpu_launches": launches * K,
+        "gpu_launches": launches * K if step_path == "graph" else K,
         "clocks": clocks,
         "e2e": {"value": ws * N * ke / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N},
@@ -868,6 +872,8 @@ def main():
                     help="time budget of the --impl reference oracle run (default 10-120 s by --steps)")
     ap.add_argument("--quick", action="store_true",
                     help="no clock warm-up loop and no CPU baseline (deterministic launch list for ncu)")
+    ap.add_argument("--step-path", default="auto", choices=["auto", "graph", "persistent"],
+                    help="film workload: how mm_step runs (mm_set_step_path)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -22,8 +22,8 @@
 // the transforms' inputs first); K_B prefetches twiddles and its M^n tile
 // (M^n was written two launches earlier, and K_A triggers its dependents
 // only once it has passed its own wait, which orders it after that writer).  Each kernel triggers
-// after its last global store (kEarlyTrigger moves K_A's trigger up to
-// its wait), so the next kernel's launch and prologue overlap its tail.
+// after its last global store (or K_A right after its wait, see
+// early_trigger), so the next kernel's launch and prologue overlap its tail.
 #pragma once
 #include <cuda_pipeline.h>
 
@@ -44,13 +44,12 @@ template <int a, int b> struct cmax { static constexpr int v = a > b ? a : b; };
 // runs (32 bytes for four rows: one sector per (c, kx)).
 constexpr int kStepRows = 4;
 
-// The plane kernel lets the x-step launch right after its own wait (true)
-// or only at its end (false).  Early: x-step blocks start on the SMs that
-// hold one plane block (their registers allow one x-step block beside a
-// plane block, two once it has left, so no SM ends up with three) and
-// fetch their twiddles and M tile while the planes run; measured 25.0
-// against 25.4 us per flushed 256x256x4 step.
-constexpr bool kEarlyTrigger = true;
+// The plane kernel lets the x-step launch right after its own wait
+// (early_trigger != 0) or only at its end.  Early: x-step blocks start on the
+// SMs that hold one plane block (their registers allow one x-step block
+// beside a plane block, two once it has left, so no SM ends up with three)
+// and fetch their twiddles and M tile while the planes run.  The plan picks
+// it where it measured faster (fast_step_early_trigger).
 
 // ------------------------------------------------------------- K_A plane --
 template <int NY, int NZ> struct PlaneLayout {
@@ -277,8 +276,8 @@ __device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, co
 // K_A as a kernel: one kx plane per CTA.
 template <int NY, int NZ>
 __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY, NZ>::THREADS <= 512) ? 2 : 1)
-    k_plane_pdl(const __grid_constant__ Geom g, const float* __restrict__ Kd, const float2* __restrict__ S, float2* __restrict__ Sh,
-                int* __restrict__ flag) {
+    k_plane_pdl(const __grid_constant__ Geom g, const float* __restrict__ Kd, const float2* __restrict__ S,
+                float2* __restrict__ Sh, int* __restrict__ flag, int early_trigger) {
     using Lay = PlaneLayout<NY, NZ>;
     using F = Fft2<NY>;
     constexpr int Q = F::Q, LY = Lay::LY, ZS = Lay::ZS, NL = Lay::NL;
@@ -310,7 +309,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
     pdl_wait();
     // S of the previous x-step is complete: the next kernel may launch and
     // run its prologue (it reads nothing this kernel writes before its own wait)
-    if constexpr (kEarlyTrigger) pdl_trigger();
+    if (early_trigger) pdl_trigger();
     if (threadIdx.x == 0) {
         proxy_fence_global();                             // S came from ordinary stores
         const float2* plane = S + (size_t)kx * NL * g.Jst;
@@ -334,7 +333,7 @@ __global__ void __launch_bounds__(PlaneLayout<NY, NZ>::THREADS, (PlaneLayout<NY,
         __syncthreads();
         return;
     }
-    if constexpr (!kEarlyTrigger) pdl_trigger();
+    if (!early_trigger) pdl_trigger();
 }
 
 // ------------------------------------------------------------- K_B xstep --

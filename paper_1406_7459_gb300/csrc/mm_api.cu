@@ -312,6 +312,11 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         g.Kd0 = c->Kd0;
         CU(configure_pass_kernels(g, c->l));
         if (c->has_fs || c->has_ss) CU(configure_step_kernels(c->fs));
+        if (c->has_fs) {
+            int sms = 0;
+            CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+            c->fs.early = fast_step_early_trigger(g, sms);
+        }
         if (c->has_persist) {
             bool usable = false;
             CU(persist_configure(g, c->fs.rb, &c->pf, &usable));
@@ -712,7 +717,7 @@ extern "C" int mm_time_passes(mm_ctx* c, int reps, double dt, void* flush, unsig
                 // pass 1 alone (the two-kernel step folds it into K_B), then K_A, K_B
                 CU(launch_pass1(c->g, c->l, c->Mbuf[p], c->S, c->stream));
                 CU(cudaEventRecord(ev[1], c->stream));
-                CU(launch_step_a(c->g, c->fs, c->Kd, c->S, c->Sh, c->flag, c->stream, false));
+                CU(launch_step_a(c->g, c->fs, c->Kd, c->S, c->Sh, c->flag, c->stream, false, 0));
                 CU(cudaEventRecord(ev[2], c->stream));
                 CU(launch_step_b(c->g, c->fs, cf, c->Sh, c->S, c->Mbuf[p], c->Mbuf[1 - p], c->flag,
                                  c->stream, false));

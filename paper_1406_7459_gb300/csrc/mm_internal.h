@@ -150,7 +150,8 @@ bool fast_lookup_plane_nz8(int ny, FastFns* f);
 // the step and H_eff, plain for H_demag); K_B = inverse x + LLG + forward x
 // from Sh into S, or its field-only variants.
 struct FastStepFns {
-    void (*ka)(Geom, const float*, const float2*, float2*, int*) = nullptr;
+    void (*ka)(Geom, const float*, const float2*, float2*, int*, int) = nullptr;
+    int early = 0;             // K_A triggers K_B right after its wait (fast_step_early_trigger)
     int ta = 0;
     size_t sa = 0;
     // x-step kernels by Pass3Mode: demag field, effective field, Euler step
@@ -166,8 +167,9 @@ bool fast_step_lookup_plane_b(int ny, int nz, FastStepFns* f);
 cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
                             const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
 cudaError_t configure_step_kernels(const FastStepFns& f);
+int fast_step_early_trigger(const Geom& g, int sms);
 cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, const float2* S, float2* Sh,
-                          int* flag, cudaStream_t s, bool pdl);
+                          int* flag, cudaStream_t s, bool pdl, int early);
 // The two-kernel evaluation of H_demag (mode kModeDemag, plain 2-D spectrum
 // Kd0) or H_eff (kModeHeff, exchange-folded Kd) of M into out, after
 // launch_pass1 has formed S from M.
