@@ -62,6 +62,7 @@ template <int NY, int NZ> struct PlaneLayout {
     static constexpr int ZS = 2 * HALF;                   // line stride
     static constexpr int HY = NY + 1;
     static constexpr int HYP = kd_row(HY);                // row of the 2-D spectrum, 16-byte multiple
+    static constexpr int KY_EVEN = (HY + 1) / 2;          // even ky' stored first in a row, then odd
     static constexpr int KT_FLOATS = HYP * NZ * 6;        // one kx slice of the 2-D spectrum,
     // [dz*6 + c][ky] as stored, so that consecutive threads (consecutive ky)
     // read consecutive words
@@ -207,6 +208,8 @@ __device__ __forceinline__ bool plane_body(const Geom& g, int kx, bool ok_in, co
         int kyp = ky;
         float sy = 1.f;
         if (2 * ky > LY) { kyp = LY - ky; sy = -1.f; }
+        // the stored row: even ky' first, then odd (same parity as ky)
+        kyp = (kyp & 1) ? Lay::KY_EVEN + (kyp >> 1) : (kyp >> 1);
         // the column's couplings: read once for the three output components
         // when registers allow (nz <= 4), else per component
         constexpr bool HOIST = NZ <= 4;

@@ -231,8 +231,9 @@ __global__ void k_tz(int nz, int Hx, int Hy, int Lz, int Hz, double scale, const
 // works with M_z' = i M_z and H_z' = i H_z, which makes every coupling real:
 // stored d_c = s_c N2_c / (Lx Ly) with s = (-1, +1, +1, -1, +1, -1) for
 // (xx, xy, xz, yy, yz, zz); H_z' takes -d_xz, -d_yz.  Layout
-// Kd[kx][dz][c][ky], dz = 0..nz-1 (negative offsets: xz, yz change sign),
-// rows of Hyp = Hy rounded up to 4 floats (zero tail), so that one kx slice
+// Kd[kx][dz][c][row], dz = 0..nz-1 (negative offsets: xz, yz change sign),
+// each row the even ky then the odd ky, Hyp = Hy rounded up to 4 floats
+// (zero tail), so that one kx slice
 // is a contiguous run of 16-byte chunks in the order the plane kernel keeps
 // it in shared memory.
 // With ex.on the exchange operator of Eq. (4) is folded in as the
@@ -244,14 +245,19 @@ __global__ void k_pack2d(int nz, int Hx, int Hy, int Hyp, double scale, const do
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t total = (size_t)6 * Hx * Hyp * nz;
     if (t >= total) return;
-    const int ky = (int)(t % Hyp);
+    // a row holds the even ky (0, 2, ..., at positions 0 .. E-1) and then the
+    // odd ky (1, 3, ..., at E .. Hy-1), E = (Hy + 1) / 2: the plane kernel's
+    // consecutive threads take ky of one parity, so they read consecutive words
+    const int pos = (int)(t % Hyp);
     const int c = (int)((t / Hyp) % 6);
     const int dz = (int)((t / ((size_t)6 * Hyp)) % nz);
     const int kx = (int)(t / ((size_t)6 * Hyp * nz));
-    if (ky >= Hy) {
+    const int E = (Hy + 1) / 2;
+    if (pos >= Hy) {
         Kd[t] = 0.f;
         return;
     }
+    const int ky = pos < E ? 2 * pos : 2 * (pos - E) + 1;
     const double v = in[(((size_t)c * nz + dz) * Hy + ky) * Hx + kx];
     const double sg = (c == 0 || c == 3 || c == 5) ? -1.0 : 1.0;
     double e = 0.0;
