@@ -348,7 +348,8 @@ template <int N, int R> struct XstepLayout {
     static constexpr int HP = 2 * HM;                     // staged positions per component
     static constexpr int HOFF = N + 8;                    // odd-kx half of a forward line, shifted by
                                                           // 64 bytes against the even half
-    static constexpr int ZS = N + HOFF;                   // forward line stride
+    static constexpr int ZS = N + HOFF + 4;               // forward line stride: the split's two row
+                                                          // pairs of a half-warp 32 bytes apart in banks
     static constexpr int MROWS = R;                        // rows of the M tile per component
     static constexpr int TW_OFF = 0, TA_OFF = L;
     static constexpr int MT_OFF = L + N;                          // float2 units; floats: 3*MROWS*N
