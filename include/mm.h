@@ -196,6 +196,20 @@ int mm_effective_field(mm_ctx *ctx, const float *M_dev, float *H_dev);
 int mm_step(mm_ctx *ctx, int n, double dt);
 
 /*
+ * mm_step_host -- n steps (n >= 0, dt > 0) from a state held in host
+ * memory, with the result written back to host memory: the same result as
+ * mm_set_m(M_in), mm_step(n, dt), mm_get_m(M_out), bit for bit, with one
+ * synchronisation.  M_in, M_out: 3*N float32 in host memory (they may be
+ * the same buffer).  On the power-of-two films' Euler step (graph path),
+ * the kernels themselves read M_in and write M_out over the host link
+ * (no staging copies) when the buffers are page-locked, or pageable on a
+ * device with coherent access to pageable host memory; otherwise the data
+ * is staged with copies.  The context's state becomes the result.  A
+ * non-finite result is reported by the next mm_sync.  Synchronises.
+ */
+int mm_step_host(mm_ctx *ctx, const float *M_in, int n, double dt, float *M_out);
+
+/*
  * mm_set_step_path -- choose how mm_step runs Euler steps: MM_STEP_AUTO
  * (default; the graph step, measured faster on GB300), MM_STEP_GRAPH or
  * MM_STEP_PERSISTENT.  The persistent step keeps

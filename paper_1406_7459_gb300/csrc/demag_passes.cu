@@ -69,12 +69,13 @@ cudaError_t configure_pass_kernels(const Geom& g, const Launch& l) {
     if (!pf) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem2);
 }
-cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s) {
+cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s, float* Mcopy) {
     if (l.fx) {
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = launch_config(dim3(3 * g.nz * (g.ny / l.fx->r1)), l.fx->t1, l.fx->s1, s, attr);
-        return cudaLaunchKernelEx(&cfg, l.fx->p1, g, M, S);
+        return cudaLaunchKernelEx(&cfg, l.fx->p1, g, M, S, Mcopy);
     }
+    if (Mcopy) return cudaErrorInvalidValue;      // the generic pass keeps no copy
     const int ntj = (g.ny + l.r1 - 1) / l.r1;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(dim3(3 * g.nz * ntj), l.t1, l.smem1, s, attr);

@@ -23,9 +23,11 @@ __host__ __device__ constexpr int pzlen(int L) { return L + L / 16 + 1; }
 // ---------------------------------------------------------------- pass 1 --
 // CTA tile: component c, layer k, rows j0..j0+R-1 (R/2 row pairs, each pair
 // one complex line).  Groups of G threads: (pair, half).
+// Mcopy (may be null): a second copy of the rows read, e.g. the device copy
+// of a state that M points to in host memory.
 template <int N, int R>
 __global__ void __launch_bounds__(R * Fft2<N>::G) k_pass1_fast(Geom g, const float* __restrict__ M,
-                                                                float2* __restrict__ S) {
+                                                                float2* __restrict__ S, float* __restrict__ Mcopy) {
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = 2 * N, ZS = pzlen(2 * N);
     constexpr int T = R * G;                              // the launch's block size
@@ -55,6 +57,15 @@ __global__ void __launch_bounds__(R * Fft2<N>::G) k_pass1_fast(Geom g, const flo
         for (int q = 0; q < P; ++q) {
             const int j = t + Q * q;
             v[q] = make_float2(__ldg(ra + j), __ldg(rb + j));
+        }
+        if (Mcopy && h == 0) {
+            float* ca = Mcopy + (ra - M);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int j = t + Q * q;
+                ca[j] = v[q].x;
+                ca[N + j] = v[q].y;
+            }
         }
         if (h) F::odd_input(v, t, tw);
         F::stepA(v, t, tw, ex + grp * F::EX, false);

@@ -366,7 +366,8 @@ template <int N, int R> struct XstepLayout {
 // Mout when Mout is given; Snext = its x spectrum); kModeHeff: Mout = H_eff
 // of M (Sh from the spectrum with the exchange stencil folded in);
 // kModeDemag: Mout = H_demag (Sh from the plain tensor spectrum, Mt unused).
-// Snext and flag are used by the step only.
+// Snext, flag and Mcopy (a second destination of M^{n+1}, may be null) are
+// used by the step only.
 //
 // The x-step work for tile `tile` (layer k, rows j0 .. j0 + R - 1): tw, ta
 // (x twiddles) and, except for kModeDemag, the tile's M^n rows Mt
@@ -377,7 +378,8 @@ template <int N, int R, int MODE, int T>
 __device__ __forceinline__ void xstep_body(const Geom& g, const LlgCoef& cf, int tile, const float2* tw,
                                            const float2* ta, float* Mt, float2* sb, float2* wk,
                                            const float2* __restrict__ Sh, float2* __restrict__ Snext,
-                                           float* __restrict__ Mout, int* __restrict__ flag) {
+                                           float* __restrict__ Mout, int* __restrict__ flag,
+                                           float* __restrict__ Mcopy = nullptr) {
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
@@ -519,6 +521,11 @@ __device__ __forceinline__ void xstep_body(const Geom& g, const LlgCoef& cf, int
             Mout[Nc + cell] = o1;
             Mout[2 * Nc + cell] = o2;
         }
+        if (Mcopy) {                                       // e.g. a host buffer, written over the link
+            Mcopy[cell] = o0;
+            Mcopy[Nc + cell] = o1;
+            Mcopy[2 * Nc + cell] = o2;
+        }
         // M^{n+1} replaces M^n in the tile (this thread read its own cell above)
         Mt[(0 * R + r) * N + i] = o0;
         Mt[(1 * R + r) * N + i] = o1;
@@ -583,8 +590,9 @@ __device__ __forceinline__ void load_mtile(const Geom& g, int tile, const float*
 // K_B as a kernel: one (layer, R rows) tile per CTA.
 template <int N, int R, int MODE>
 __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
-    k_xstep_pdl(const __grid_constant__ Geom g, const __grid_constant__ LlgCoef cf, const float2* __restrict__ Sh, float2* __restrict__ Snext,
-                const float* __restrict__ M, float* __restrict__ Mout, int* __restrict__ flag) {
+    k_xstep_pdl(const __grid_constant__ Geom g, const __grid_constant__ LlgCoef cf, const float2* __restrict__ Sh,
+                float2* __restrict__ Snext, const float* __restrict__ M, float* __restrict__ Mout,
+                int* __restrict__ flag, float* __restrict__ Mcopy) {
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int L = Lay::L;
@@ -606,7 +614,7 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     if constexpr (MODE != kModeDemag) load_mtile<N, R, T>(g, blockIdx.x, M, Mt);
     __pipeline_commit();
     pdl_wait();
-    xstep_body<N, R, MODE, T>(g, cf, blockIdx.x, tw, ta, Mt, sb, wk, Sh, Snext, Mout, flag);
+    xstep_body<N, R, MODE, T>(g, cf, blockIdx.x, tw, ta, Mt, sb, wk, Sh, Snext, Mout, flag, Mcopy);
     __syncthreads();
     pdl_trigger();
 }

@@ -65,10 +65,10 @@ cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, 
 }
 
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
-                          const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
+                          const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl, float* Mcopy) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, attr, pdl);
-    return cudaLaunchKernelEx(&cfg, f.kb[kModeStep], g, c, Sh, S, M, Mout, flag);
+    return cudaLaunchKernelEx(&cfg, f.kb[kModeStep], g, c, Sh, S, M, Mout, flag, Mcopy);
 }
 
 cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, int mode, const float* Kd,
@@ -77,17 +77,18 @@ cudaError_t launch_field_pdl(const Geom& g, const FastStepFns& f, const LlgCoef&
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / f.rb)), f.tb, f.sb, s, attr, true);
-    return cudaLaunchKernelEx(&cfg, f.kb[mode], g, c, (const float2*)Sh, (float2*)nullptr, M, out, (int*)nullptr);
+    return cudaLaunchKernelEx(&cfg, f.kb[mode], g, c, (const float2*)Sh, (float2*)nullptr, M, out, (int*)nullptr,
+                              (float*)nullptr);
 }
 
 // K_A then K_B; with `pdl` both carry the programmatic-serialisation launch
 // attribute so each may start while its predecessor drains (each kernel
 // waits on griddepcontrol before reading what the predecessor wrote).
 cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
-                            const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl) {
+                            const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl, float* Mcopy) {
     cudaError_t e = launch_step_a(g, f, g.Kd, S, Sh, flag, s, pdl, f.early);
     if (e != cudaSuccess) return e;
-    return launch_step_b(g, f, c, Sh, S, M, Mout, flag, s, pdl);
+    return launch_step_b(g, f, c, Sh, S, M, Mout, flag, s, pdl, Mcopy);
 }
 
 }  // namespace mmk

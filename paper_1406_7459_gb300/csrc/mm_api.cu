@@ -636,6 +636,73 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
     return MM_OK;
 }
 
+// A host buffer's address as kernels may use it: page-locked memory mapped
+// into the device's address space, or, where the device reaches pageable
+// host memory coherently (cudaDevAttrPageableMemoryAccess, e.g. over a
+// cache-coherent chip-to-chip link), the address itself; nullptr otherwise
+// (the caller then stages the data with copies).
+static void* kernel_view(void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    if (a.type == cudaMemoryTypeUnregistered) {
+        int dev = 0, pageable = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess && pageable)
+            return p;
+        cudaGetLastError();
+    }
+    return nullptr;
+}
+
+extern "C" int mm_step_host(mm_ctx* c, const float* M_in, int n, double dt, float* M_out) {
+    if (!c || !M_in || !M_out) return fail(MM_EINVAL, "null argument");
+    if (n < 0) return fail(MM_EINVAL, "n must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
+    const size_t bytes = sizeof(float) * 3 * (size_t)c->g.N;
+    const bool fast = c->has_fs && c->method == MM_INTEGRATOR_EULER && !uses_persist(c) && n > 0 &&
+                      !is_device_ptr(M_in) && !is_device_ptr(M_out);
+    if (!fast) {
+        // copies around the ordinary step, one synchronisation at the end
+        CU(cudaMemcpyAsync(c->Mbuf[c->cur], M_in, bytes, cudaMemcpyDefault, c->stream));
+        CU(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+        c->spec_valid = false;
+        int rc = mm_step(c, n, dt);
+        if (rc != MM_OK) return rc;
+        CU(cudaMemcpyAsync(M_out, c->Mbuf[c->cur], bytes, cudaMemcpyDefault, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        return MM_OK;
+    }
+    const float* in = (const float*)kernel_view(const_cast<float*>(M_in));
+    float* out = (float*)kernel_view(M_out);
+    if (!in) {
+        CU(cudaMemcpyAsync(c->Mbuf[c->cur], M_in, bytes, cudaMemcpyHostToDevice, c->stream));
+        in = c->Mbuf[c->cur];
+    }
+    CU(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    // the x transform of the starting state reads it where it lies and
+    // leaves a device copy for the updates; the last step's update writes
+    // the new state to the context and to the caller's buffer
+    float* cp = in == c->Mbuf[c->cur] ? nullptr : c->Mbuf[c->cur];
+    CU(launch_pass1(c->g, c->l, in, c->S, c->stream, cp));
+    const LlgCoef cf = make_coef(c, dt);
+    int p = c->cur;
+    for (int s = 0; s < n; ++s) {
+        const float* Mn = c->Mbuf[p];
+        float* copy = (s == n - 1) ? out : nullptr;
+        CU(launch_step_pdl(c->g, c->fs, cf, c->S, c->Sh, Mn, c->Mbuf[1 - p], c->flag, c->stream, true, copy));
+        p = 1 - p;
+    }
+    c->cur = p;
+    c->spec_valid = true;
+    if (!out) CU(cudaMemcpyAsync(M_out, c->Mbuf[p], bytes, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return MM_OK;
+}
+
 static int read_flag(mm_ctx* c) {
     int f = 0;
     CU(cudaMemcpy(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost));

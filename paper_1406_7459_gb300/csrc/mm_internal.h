@@ -102,7 +102,9 @@ void plan_twiddles(int L, float2* out);
 int set_error(int code, const char* msg);
 
 // Launchers (demag_passes.cu).  All asynchronous on `s`.
-cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s);
+// Mcopy (compile-time x passes only, may be null): also copy M there.
+cudaError_t launch_pass1(const Geom& g, const Launch& l, const float* M, float2* S, cudaStream_t s,
+                         float* Mcopy = nullptr);
 cudaError_t launch_plane(const Geom& g, const Launch& l, float2* S, cudaStream_t s);
 cudaError_t launch_pass3(const Geom& g, const Launch& l, const LlgCoef& c, int mode, const float2* S,
                          const float* M, float* out, int* flag, cudaStream_t s);
@@ -114,7 +116,7 @@ PlaneFn plane_fn_mid(int Lz);     // plane_mid.cu
 
 // Compile-time specialised kernels for power-of-two grids (fast_*.cu).
 struct FastFns {
-    void (*p1)(Geom, const float*, float2*) = nullptr;
+    void (*p1)(Geom, const float*, float2*, float*) = nullptr;
     int r1 = 0, t1 = 0;
     size_t s1 = 0;
     void (*pl)(Geom, float2*) = nullptr;
@@ -155,7 +157,8 @@ struct FastStepFns {
     int ta = 0;
     size_t sa = 0;
     // x-step kernels by Pass3Mode: demag field, effective field, Euler step
-    void (*kb[3])(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*) = {nullptr, nullptr, nullptr};
+    void (*kb[3])(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*, float*) = {nullptr, nullptr,
+                                                                                               nullptr};
     int rb = 0, tb = 0;
     size_t sb = 0;
 };
@@ -165,7 +168,8 @@ bool fast_step_lookup_plane_b(int ny, int nz, FastStepFns* f);
 // K_A reads the x half-spectrum S and writes its output to Sh; K_B reads Sh
 // and writes the next step's S.
 cudaError_t launch_step_pdl(const Geom& g, const FastStepFns& f, const LlgCoef& c, float2* S, float2* Sh,
-                            const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
+                            const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl,
+                            float* Mcopy = nullptr);
 cudaError_t configure_step_kernels(const FastStepFns& f);
 int fast_step_early_trigger(const Geom& g, int sms);
 cudaError_t launch_step_a(const Geom& g, const FastStepFns& f, const float* Kd, const float2* S, float2* Sh,
@@ -201,9 +205,9 @@ constexpr long long kGridWaitLimit = 1LL << 20;
 // kernel of mode `mode` in place on S (S -> S, M -> out).
 cudaError_t launch_split_xstep(const Geom& g, const FastSplitFns& f2, const FastStepFns& fs, const LlgCoef& c,
                                int mode, const float* Kt, float2* S, const float* M, float* out, int* flag,
-                               cudaStream_t s);
+                               cudaStream_t s, float* Mcopy = nullptr);
 cudaError_t launch_step_b(const Geom& g, const FastStepFns& f, const LlgCoef& c, const float2* Sh, float2* S,
-                          const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl);
+                          const float* M, float* Mout, int* flag, cudaStream_t s, bool pdl, float* Mcopy = nullptr);
 
 // Pass 2 for thick samples (split_kernels.cu); the spectrum row stride is Ly.
 cudaError_t launch_split_plane(const Geom& g, float2* S, cudaStream_t s);

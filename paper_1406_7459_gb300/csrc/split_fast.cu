@@ -345,7 +345,7 @@ cudaError_t launch_fast_split(const Geom& g, const FastSplitFns& f, const float*
 
 cudaError_t launch_split_xstep(const Geom& g, const FastSplitFns& f2, const FastStepFns& fs, const LlgCoef& c,
                                int mode, const float* Kt, float2* S, const float* M, float* out, int* flag,
-                               cudaStream_t s) {
+                               cudaStream_t s, float* Mcopy) {
     cudaError_t e = launch_fast_split(g, f2, Kt, S, s);
     if (e != cudaSuccess) return e;
     // the x-step kernel reads its tile of S (all kx of R rows of a layer)
@@ -353,7 +353,8 @@ cudaError_t launch_split_xstep(const Geom& g, const FastSplitFns& f2, const Fast
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config(dim3(g.nz * (g.ny / fs.rb)), fs.tb, fs.sb, s, attr);
     return cudaLaunchKernelEx(&cfg, fs.kb[mode], g, c, (const float2*)S, mode == kModeStep ? S : (float2*)nullptr,
-                              M, out, mode == kModeStep ? flag : (int*)nullptr);
+                              M, out, mode == kModeStep ? flag : (int*)nullptr,
+                              mode == kModeStep ? Mcopy : (float*)nullptr);
 }
 
 }  // namespace mmk

@@ -44,6 +44,7 @@ _PROTOS = {
     "mm_demag_field": (_c_int, [_vp, _vp, _vp]),
     "mm_effective_field": (_c_int, [_vp, _vp, _vp]),
     "mm_step": (_c_int, [_vp, _c_int, _c_double]),
+    "mm_step_host": (_c_int, [_vp, _vp, _c_int, _c_double, _vp]),
     "mm_set_step_path": (_c_int, [_vp, _c_int]),
     "mm_get_step_path": (_c_int, [_vp]),
     "mm_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
@@ -206,6 +207,14 @@ def mm_effective_field(ctx, M, H):
 
 def mm_step(ctx, n, dt):
     _check(lib().mm_step(ctx.handle, int(n), float(dt)))
+
+
+def mm_step_host(ctx, M_in, n, dt, M_out):
+    """n steps from the host array M_in (numpy float32 or a CPU torch tensor,
+    3*N) into the host array M_out (may be M_in)."""
+    N3 = 3 * ctx.N
+    _check(lib().mm_step_host(ctx.handle, _vp(_ptr(M_in, N3)), int(n), float(dt), _vp(_ptr(M_out, N3))))
+    return M_out
 
 
 def mm_set_step_path(ctx, path):
