@@ -641,7 +641,7 @@ def run_batch(args, rank, ws):
                           "one_context_at_a_time_cells_steps_per_s": cells / (single_ms * 1e-3),
                           "batching_gain": single_ms / batch_ms,
                           "autotune_choice": {"rows_pass1": choice[0], "rows_pass3": choice[1],
-                                              "threads": choice[2]},
+                                              "threads": choice[2], "planes_per_cta": choice[3]},
                           "autotune_ms_per_candidate": tune_ms,
                           "l2": "working set larger than L2; steps back to back"}))
     return 0

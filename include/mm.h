@@ -331,13 +331,15 @@ int mm_batch_set_path(mm_batch *b, int path);
 int mm_batch_set_wait_limit(mm_batch *b, long long polls);
 long long mm_batch_cells(const mm_batch *b);              /* total cells, or -1 */
 /*
- * mm_batch_autotune -- time the candidate tile shapes (rows per CTA of the
- * x passes, threads per CTA) on this batch with steps of size dt, keep the
- * fastest, and restore the state (tuning does not advance the samples).
- * choice (may be NULL): {rows pass 1, rows pass 3, threads}; ms_out (may be
- * NULL): 12 floats, mean ms per step of each candidate.  Synchronises.
+ * mm_batch_autotune -- time the candidate tile shapes on this batch with
+ * steps of size dt, keep the fastest, and restore the state (tuning does not
+ * advance the samples): first the rows per CTA of the x passes and the
+ * threads per CTA (12 candidates), then, with those, the kx planes per CTA
+ * of the plane pass (1, 2, 4, 8).  choice (may be NULL): {rows pass 1, rows
+ * pass 3, threads, planes per CTA}; ms_out (may be NULL): 16 floats, mean ms
+ * per step of each candidate in that order.  Synchronises.
  */
-int mm_batch_autotune(mm_batch *b, double dt, int choice[3], float *ms_out);
+int mm_batch_autotune(mm_batch *b, double dt, int choice[4], float *ms_out);
 
 /* ------------------------------------------------------------------------
  * Learned surrogate of the demag field (not in the paper): a Fourier neural

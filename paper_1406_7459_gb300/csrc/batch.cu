@@ -39,6 +39,7 @@ struct BatchDesc {
     float* M1;
     float2* S;
     int r1, r3;
+    int r2;                                   // kx planes per plane-pass CTA
 };
 
 __device__ __forceinline__ int find_sample(const int* __restrict__ pre, int ns, int b) {
@@ -58,18 +59,24 @@ __global__ void __launch_bounds__(256) k_batch_pass1(const BatchDesc* __restrict
     pass1_body(b.g, b.r1, b.r1 / 2, par ? b.M1 : b.M0, b.S, blockIdx.x - __ldg(pre + s));
 }
 
+// plane-pass tile `tile` of a sample: r2 consecutive kx planes (fewer at
+// the end), all their lines transformed together
+__device__ __forceinline__ void batch_plane_tile(const BatchDesc& b, int tile) {
+    const int kx0 = tile * b.r2;
+    const int np = min(b.r2, b.g.Hx - kx0);
+    const int nl = 3 * b.g.nz * np;
+    switch (b.g.Lz) {
+        case 1: plane_body_multi<1>(b.g, nl, b.S, kx0, np); break;
+        case 4: plane_body_multi<4>(b.g, nl, b.S, kx0, np); break;
+        case 5: plane_body_multi<5>(b.g, nl, b.S, kx0, np); break;
+        default: plane_body_multi<8>(b.g, nl, b.S, kx0, np); break;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_batch_plane(const BatchDesc* __restrict__ d, const int* __restrict__ pre,
                                                       int ns) {
     const int s = find_sample(pre, ns, blockIdx.x);
-    const BatchDesc& b = d[s];
-    const int tile = blockIdx.x - __ldg(pre + s);
-    const int nl = 3 * b.g.nz;
-    switch (b.g.Lz) {
-        case 1: plane_body<1>(b.g, nl, b.S, tile); break;
-        case 4: plane_body<4>(b.g, nl, b.S, tile); break;
-        case 5: plane_body<5>(b.g, nl, b.S, tile); break;
-        default: plane_body<8>(b.g, nl, b.S, tile); break;
-    }
+    batch_plane_tile(d[s], blockIdx.x - __ldg(pre + s));
 }
 
 __global__ void __launch_bounds__(256) k_batch_pass3(const BatchDesc* __restrict__ d, const int* __restrict__ pre,
@@ -80,16 +87,6 @@ __global__ void __launch_bounds__(256) k_batch_pass3(const BatchDesc* __restrict
     cf.dt = dt;
     pass3_body<kModeStep>(b.g, b.r3, 3 * b.r3 / 2, cf, b.S, par ? b.M1 : b.M0, par ? b.M0 : b.M1, flag,
                           blockIdx.x - __ldg(pre + s));
-}
-
-__device__ __forceinline__ void batch_plane_tile(const BatchDesc& b, int tile) {
-    const int nl = 3 * b.g.nz;
-    switch (b.g.Lz) {
-        case 1: plane_body<1>(b.g, nl, b.S, tile); break;
-        case 4: plane_body<4>(b.g, nl, b.S, tile); break;
-        case 5: plane_body<5>(b.g, nl, b.S, tile); break;
-        default: plane_body<8>(b.g, nl, b.S, tile); break;
-    }
 }
 
 // n steps of every sample in one cooperative launch.  Work queue 0 holds
@@ -162,7 +159,7 @@ struct mm_batch {
     int* flag = nullptr;
     int tiles[3] = {0, 0, 0};
     size_t smem[3] = {0, 0, 0};
-    int threads = 256, r1 = 4, r3 = 2;
+    int threads = 256, r1 = 4, r3 = 2, r2 = 1;
     int par = 0;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     double exec_dt[2] = {0, 0};
@@ -217,9 +214,10 @@ static int batch_layout(mm_batch* b) {
         const Geom& g = d.g;
         d.r1 = b->r1;
         d.r3 = b->r3;
+        d.r2 = b->r2;
         d.cf = batch_coef(b, s);
         const int t1 = 3 * g.nz * ((g.ny + b->r1 - 1) / b->r1);
-        const int t2 = g.Hx;
+        const int t2 = (g.Hx + b->r2 - 1) / b->r2;
         const int t3 = g.nz * ((g.ny + b->r3 - 1) / b->r3);
         pre[0 * (b->ns + 1) + s] = acc[0];
         pre[1 * (b->ns + 1) + s] = acc[1];
@@ -228,7 +226,8 @@ static int batch_layout(mm_batch* b) {
         acc[1] += t2;
         acc[2] += t3;
         const size_t lx = (size_t)padded_len(g.Lx) * sizeof(float2), ly = (size_t)padded_len(g.Ly) * sizeof(float2);
-        const size_t a1 = 2 * (size_t)(b->r1 / 2) * lx, a2 = 2 * (size_t)3 * g.nz * ly, a3 = 2 * (size_t)(3 * b->r3 / 2) * lx;
+        const size_t a1 = 2 * (size_t)(b->r1 / 2) * lx, a2 = 2 * (size_t)3 * g.nz * b->r2 * ly,
+                     a3 = 2 * (size_t)(3 * b->r3 / 2) * lx;
         sm[0] = a1 > sm[0] ? a1 : sm[0];
         sm[1] = a2 > sm[1] ? a2 : sm[1];
         sm[2] = a3 > sm[2] ? a3 : sm[2];
@@ -536,7 +535,7 @@ extern "C" int mm_batch_sync(mm_batch* b) {
 
 extern "C" long long mm_batch_cells(const mm_batch* b) { return b ? b->cells : -1; }
 
-extern "C" int mm_batch_autotune(mm_batch* b, double dt, int choice[3], float* ms_out) {
+extern "C" int mm_batch_autotune(mm_batch* b, double dt, int choice[4], float* ms_out) {
     if (!b || !(dt > 0.0)) return set_error(MM_EINVAL, "null batch or dt <= 0");
     // keep the state: tuning steps run on a saved copy
     float* save = nullptr;
@@ -552,6 +551,7 @@ extern "C" int mm_batch_autotune(mm_batch* b, double dt, int choice[3], float* m
     float best = 1e30f;
     int bi = 0;
     int rc = MM_OK;
+    b->r2 = 1;
     for (int c = 0; c < nc && rc == MM_OK; ++c) {
         b->r1 = cand[c][0];
         b->r3 = cand[c][1];
@@ -577,12 +577,43 @@ extern "C" int mm_batch_autotune(mm_batch* b, double dt, int choice[3], float* m
             bi = c;
         }
     }
+    // second stage: kx planes per plane-pass CTA with the best x-pass shapes
+    static const int cand2[] = {1, 2, 4, 8};
+    int b2 = 0;
+    float best2 = 1e30f;
+    for (int c = 0; c < 4 && rc == MM_OK; ++c) {
+        b->r1 = cand[bi][0];
+        b->r3 = cand[bi][1];
+        b->threads = cand[bi][2];
+        b->r2 = cand2[c];
+        rc = batch_layout(b);
+        if (rc != MM_OK) break;
+        rc = batch_enqueue(b, b->par, dt, b->stream);            // warm-up
+        if (rc != MM_OK) break;
+        b->par = 1 - b->par;
+        cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < 3 && rc == MM_OK; ++k) {
+            rc = batch_enqueue(b, b->par, dt, b->stream);
+            b->par = 1 - b->par;
+        }
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        if (ms_out) ms_out[nc + c] = ms;
+        if (ms < best2) {
+            best2 = ms;
+            b2 = c;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc == MM_OK) {
         b->r1 = cand[bi][0];
         b->r3 = cand[bi][1];
         b->threads = cand[bi][2];
+        b->r2 = cand2[b2];
         rc = batch_layout(b);
     }
     cudaMemcpyAsync(b->par ? b->M1 : b->M0, save, sizeof(float) * b->mtotal, cudaMemcpyDeviceToDevice, b->stream);
@@ -595,6 +626,7 @@ extern "C" int mm_batch_autotune(mm_batch* b, double dt, int choice[3], float* m
         choice[0] = b->r1;
         choice[1] = b->r3;
         choice[2] = b->threads;
+        choice[3] = b->r2;
     }
     return MM_OK;
 }

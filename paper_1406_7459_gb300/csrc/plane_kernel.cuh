@@ -43,30 +43,39 @@ __device__ __forceinline__ void small_dft(float2 (&a)[LZ], int nin, int nout, co
     for (int q = 0; q < LZ; ++q) a[q] = o[q];
 }
 
+// np consecutive kx planes from kx0 (their lines are contiguous in S):
+// every line of the np planes transformed together (one pass of barriers
+// for all of them), then the z DFTs and the product for each (kx, ky).
+// Each line's transform and each (kx, ky)'s product are the arithmetic of
+// one plane alone, so any np gives the same bits.  Shared memory: two
+// buffers of np 3 nz lines of padded_len(Ly).
 template <int LZ>
-__device__ __forceinline__ void plane_body(const Geom& g, int group, float2* __restrict__ S, int kx) {
+__device__ __forceinline__ void plane_body_multi(const Geom& g, int group, float2* __restrict__ S, int kx0, int np) {
     extern __shared__ float2 sm[];
     const int lstride = padded_len(g.Ly);
     const int nz = g.nz;
     const int nl = 3 * nz;
-    float2* plane = S + (size_t)kx * nl * g.Jst;
+    const int nlt = np * nl;
+    float2* plane = S + (size_t)kx0 * nl * g.Jst;
 
-    for (int idx = threadIdx.x; idx < nl * g.ny; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nlt * g.ny; idx += blockDim.x) {
         const int l = idx / g.ny;
         const int j = idx - l * g.ny;
         sm[l * lstride + padi(j)] = plane[(size_t)l * g.Jst + j];
     }
-    fft_lines(sm, sm + nl * lstride, lstride, nl, group, g.py, g.twy, g.ny, false);
+    fft_lines(sm, sm + nlt * lstride, lstride, nlt, group, g.py, g.twy, g.ny, false);
 
-    const float* Kp = g.Kt + (size_t)kx * g.Hz * g.Hy * 6;
-    for (int ky = threadIdx.x; ky < g.Ly; ky += blockDim.x) {
+    for (int t = threadIdx.x; t < np * g.Ly; t += blockDim.x) {
+        const int pp = t / g.Ly, ky = t - pp * g.Ly;
+        const float* Kp = g.Kt + (size_t)(kx0 + pp) * g.Hz * g.Hy * 6;
+        float2* sp = sm + (size_t)pp * nl * lstride;
         float2 m[3][LZ];
         const int e = padi(ky);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
 #pragma unroll
             for (int k = 0; k < LZ; ++k)
-                m[c][k] = (k < nz) ? sm[(c * nz + k) * lstride + e] : make_float2(0.f, 0.f);
+                m[c][k] = (k < nz) ? sp[(c * nz + k) * lstride + e] : make_float2(0.f, 0.f);
             small_dft<LZ>(m[c], nz, LZ, g.twz, false);
         }
         int kyp = ky;
@@ -90,16 +99,21 @@ __device__ __forceinline__ void plane_body(const Geom& g, int group, float2* __r
             small_dft<LZ>(m[c], LZ, nz, g.twz, true);
 #pragma unroll
             for (int k = 0; k < LZ; ++k)
-                if (k < nz) sm[(c * nz + k) * lstride + e] = m[c][k];
+                if (k < nz) sp[(c * nz + k) * lstride + e] = m[c][k];
         }
     }
-    fft_lines(sm, sm + nl * lstride, lstride, nl, group, g.py, g.twy, g.Ly, true);
+    fft_lines(sm, sm + nlt * lstride, lstride, nlt, group, g.py, g.twy, g.Ly, true);
 
-    for (int idx = threadIdx.x; idx < nl * g.ny; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nlt * g.ny; idx += blockDim.x) {
         const int l = idx / g.ny;
         const int j = idx - l * g.ny;
         plane[(size_t)l * g.Jst + j] = sm[l * lstride + padi(j)];
     }
+}
+
+template <int LZ>
+__device__ __forceinline__ void plane_body(const Geom& g, int group, float2* __restrict__ S, int kx) {
+    plane_body_multi<LZ>(g, group, S, kx, 1);
 }
 
 template <int LZ>

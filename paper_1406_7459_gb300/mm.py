@@ -368,8 +368,8 @@ def mm_batch_cells(b):
 
 
 def mm_batch_autotune(b, dt):
-    choice = (ctypes.c_int * 3)()
-    ms = (ctypes.c_float * 12)()
+    choice = (ctypes.c_int * 4)()
+    ms = (ctypes.c_float * 16)()
     _check(lib().mm_batch_autotune(b.handle, float(dt), choice, ms))
     return tuple(choice), list(ms)
 

@@ -68,7 +68,8 @@ def test_autotune_keeps_state_and_results():
     mm.mm_batch_get_m(b, after)
     assert torch.equal(before, after)
     assert choice[0] in (2, 4, 8) and choice[1] in (2, 4) and choice[2] in (128, 256)
-    assert all(m > 0 for m in ms)
+    assert choice[3] in (1, 2, 4, 8)
+    assert len(ms) == 16 and all(m > 0 for m in ms)
     mm.mm_batch_step(b, 3, 5e-14)
     mm.mm_batch_get_m(b, after)
     mm.mm_batch_sync(b)
