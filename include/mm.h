@@ -300,10 +300,12 @@ int mm_time_passes(mm_ctx *ctx, int reps, double dt, void *flush, unsigned long 
  * size slowness on launch overhead, which batching removes).  Sample s has
  * its own grid (nz <= 4), cell, material, field and tensor spectrum; every
  * call of mm_batch_step advances all samples by forward-Euler steps of the
- * same dt, with three batched kernels per step replayed from a CUDA graph,
- * or (mm_batch_set_path MM_STEP_PERSISTENT) as one cooperative launch for up
- * to 1024 steps whose blocks take (sample, tile) items from a work queue per
- * pass, the passes separated by bounded grid barriers (same arithmetic).
+ * same dt, with two batched kernels per step (the plane pass; the update,
+ * which also forms the next step's x spectra) replayed from a CUDA graph
+ * after one x transform of a new state, or (mm_batch_set_path
+ * MM_STEP_PERSISTENT) as one cooperative launch for up to 1024 steps whose
+ * blocks take (sample, tile) items from a work queue per pass, the passes
+ * separated by bounded grid barriers (same arithmetic).
  * M arrays of a batch are the samples' SoA blocks back to back (sample s
  * starts at float offset sum_{t<s} 3 N_t).
  * ------------------------------------------------------------------------ */

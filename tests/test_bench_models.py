@@ -81,13 +81,13 @@ def test_batch_byte_model_uses_the_plan_lengths():
     grids = [(256, 256, 4), (200, 60, 3), (17, 33, 1)]
     by = bench.batch_bytes(grids)
     g3 = sum(bench.algorithmic_bytes(g)["step3"] for g in grids[:1])
-    assert by["graph"] > g3 and by["persistent"] < by["graph"]
+    assert by["three_pass"] > g3 and by["persistent"] == by["graph"] < by["three_pass"]
     nx, ny, nz = 200, 60, 3
     X = (400 // 2 + 1) * ny * nz
     Ks = (400 // 2 + 1) * (120 // 2 + 1) * (5 // 2 + 1)          # Lz = 5 for nz = 3
     one = bench.batch_bytes([(nx, ny, nz)])
-    assert one["graph"] == 36 * nx * ny * nz + 96 * X + 24 * Ks
-    assert one["graph"] - one["persistent"] == 12 * nx * ny * nz
+    assert one["three_pass"] == 36 * nx * ny * nz + 96 * X + 24 * Ks
+    assert one["three_pass"] - one["graph"] == 12 * nx * ny * nz
 
 
 def test_bench_truncation_floor_equals_the_oracle_floor():
