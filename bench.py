@@ -103,7 +103,7 @@ def alu_peak_tflops(sm_mhz):
 
 # Sources of the two step kernels: the DRAM traffic recorded under profiles/
 # is reported only while these files hash to the value recorded with it.
-STEP_KERNEL_SOURCES = ("fast_step.cuh", "fast_fft.cuh", "fft_device.cuh", "fast_passes.cuh",
+STEP_KERNEL_SOURCES = ("fast_step.cuh", "fast_fft.cuh", "fft_device.cuh", "fast_passes.cuh", "bulk_copy.cuh",
                        "fast_step_x.cu", "fast_step_plane_a.cu", "fast_step_plane_b.cu")
 
 
@@ -315,6 +315,8 @@ def run_gpu(args, rank, ws):
     mm.mm_set_step_path(ctx, {"auto": mm.MM_STEP_AUTO, "graph": mm.MM_STEP_GRAPH,
                               "persistent": mm.MM_STEP_PERSISTENT}[args.step_path])
     step_path = "persistent" if mm.mm_get_step_path(ctx) == mm.MM_STEP_PERSISTENT else "graph"
+    if args.tiled_copies:
+        mm.mm_set_tiled_copies(ctx, args.tiled_copies)
     mm.mm_set_field(ctx, w["H_ext"])
     M0 = inputs.uniform_m(GRID, w["Ms"], w["start"]).reshape(-1)
     mm.mm_set_m(ctx, torch.from_numpy(M0).cuda())
@@ -437,6 +439,7 @@ def run_gpu(args, rank, ws):
         "pass_ms": passes,
         "launches_per_step": launches if step_path == "graph" else "one launch per mm_step call",
         "step_path": step_path,
+        "xstep_tiled_copies": mm.mm_get_tiled_copies(ctx),
         "steady_state_l2_resident": {"ms_per_step": warm_ms, "cells_steps_per_s": ws * N / (warm_ms * 1e-3)},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -873,6 +876,8 @@ def main():
                     help="time budget of the --impl reference oracle run (default 10-120 s by --steps)")
     ap.add_argument("--quick", action="store_true",
                     help="no clock warm-up loop and no CPU baseline (deterministic launch list for ncu)")
+    ap.add_argument("--tiled-copies", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="x-step spectrum gather (1) / scatter (2) as tiled tensor copies (film workload)")
     ap.add_argument("--step-path", default="auto", choices=["auto", "graph", "persistent"],
                     help="film workload: how mm_step runs (mm_set_step_path)")
     args = ap.parse_args()

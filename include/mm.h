@@ -69,6 +69,14 @@ enum {
     MM_STEP_PERSISTENT = 2     /* one cooperative launch for many steps            */
 };
 
+/* How the x-step kernel of the graph step moves its spectrum tiles
+ * (mm_set_tiled_copies): bits that make the gather from the plane kernel's
+ * output, and the scatter of the next spectrum, tiled tensor copies. */
+enum {
+    MM_TILED_GATHER = 1,
+    MM_TILED_SCATTER = 2
+};
+
 /*
  * mm_create -- build a solver context; the tensor set-up happens here, once
  * (Sec. 3: the tensor FFT "carried out at the beginning of simulation").
@@ -224,6 +232,23 @@ int mm_set_step_path(mm_ctx *ctx, int path);
 /* mm_get_step_path -- MM_STEP_PERSISTENT or MM_STEP_GRAPH: how the next
  * mm_step will run, or a negative error code. */
 int mm_get_step_path(const mm_ctx *ctx);
+
+/*
+ * mm_set_tiled_copies -- how the x-step kernel of the two-kernel step
+ * (power-of-two films up to nx = 256) moves the transposed spectrum of the
+ * per-axis transforms (Sec. 3, Eqs. (14)-(16)): 0 (default) with 16-byte
+ * asynchronous copies issued by every thread and plain stores; a mask of
+ * MM_TILED_GATHER / MM_TILED_SCATTER makes the gather of the tile's
+ * 3 (nx + 1) runs of 32 bytes, or the scatter of the next spectrum, one
+ * tiled tensor copy of a 4-D box per block.  Same arithmetic, same result
+ * bits; the default measured faster on GB300.  Mask bits outside the two:
+ * MM_EINVAL; a nonzero mask for a grid without the tiled form:
+ * MM_EUNSUPPORTED.  Takes effect from the next step or field evaluation.
+ */
+int mm_set_tiled_copies(mm_ctx *ctx, int mask);
+
+/* mm_get_tiled_copies -- the mask in effect, or a negative error code. */
+int mm_get_tiled_copies(const mm_ctx *ctx);
 
 /*
  * mm_set_wait_limit -- a diagnostic: the number of polls a grid-barrier

@@ -13,6 +13,7 @@
 // word, waits once more (again bounded) for its copies in flight, so that no
 // copy lands in shared memory after the block has left, and returns.
 #pragma once
+#include <cuda.h>   // CUtensorMap (the type only; maps are encoded on the host)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -55,6 +56,36 @@ __device__ __forceinline__ void proxy_fence_global() { asm volatile("fence.proxy
 // The same for shared memory that the block has accessed with ordinary loads
 // and stores (after a block barrier) and that bulk copies overwrite next.
 __device__ __forceinline__ void proxy_fence_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Tiled tensor copies (cp.async.bulk.tensor) through a tensor map that is
+// a __grid_constant__ kernel parameter.  The shared-memory side is the box
+// of the map, innermost dimension fastest, starting on 128 bytes; the
+// innermost coordinate times the element size is a multiple of 16 bytes.
+__device__ __forceinline__ void tensor_prefetch(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+
+// 4-D box at (x0, x1, x2, x3) from global memory to shared `dst`, counted on `bar`.
+__device__ __forceinline__ void tensor_g2s_4d(uint32_t dst, const CUtensorMap* map, int x0, int x1, int x2, int x3,
+                                              uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(map), "r"(x0), "r"(x1), "r"(x2), "r"(x3), "r"(bar)
+        : "memory");
+}
+
+// 4-D box from shared `src` to global memory at (x0, x1, x2, x3), in this
+// thread's current bulk group (bulk_commit, then bulk_wait_all before the
+// shared memory is reused or the block leaves).
+__device__ __forceinline__ void tensor_s2g_4d(const CUtensorMap* map, int x0, int x1, int x2, int x3, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                 "r"(x0), "r"(x1), "r"(x2), "r"(x3), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Completion (writes done) of every bulk group this thread committed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Bounded wait for the phase of parity `parity` of `bar` to complete.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {

@@ -358,8 +358,25 @@ template <int N, int R> struct XstepLayout {
     static constexpr int SB_C = cmax<3 * HP * R, 3 * R * N / 2>::v;
     static constexpr int W_OFF = SB_OFF + ((SB_C + 1) / 2) * 2;
     static constexpr int W_C = cmax<cmax<2 * NL * F::EX, NL * L>::v, NL * ZS>::v;
-    static constexpr size_t BYTES = sizeof(float2) * (W_OFF + W_C);
+    static constexpr int BAR_OFF = W_OFF + W_C;                   // mbarrier of the tiled gather
+    static constexpr size_t BYTES = sizeof(float2) * (BAR_OFF + 2);
+    // one tile's box of the tiled gather / scatter: 2R floats of each of
+    // the 3 HP (c, parity, kx / 2) positions
+    static constexpr uint32_t BOX_BYTES = 3 * HP * R * sizeof(float2);
+    static_assert((SB_OFF * sizeof(float2)) % 128 == 0, "staged spectrum on 128 bytes (tiled copies)");
     static constexpr int THREADS = cmax<2 * NL * F::G, 128>::v;
+};
+
+// Tiled tensor copies of the x-step's spectrum traffic: `in` gathers the
+// tile's rows of Sh into sb (one box per tile, counted on the shared
+// mbarrier `bar`), `out` scatters the next spectrum from sb to Snext.  The
+// box of both maps is the layout sb has anyway, [c][kx parity][kx / 2][2R
+// floats of rows j0 ..], so the arithmetic between them is unchanged.  Null
+// maps: 16-byte asynchronous copies per thread and plain stores.
+struct XTma {
+    const CUtensorMap* in = nullptr;
+    const CUtensorMap* out = nullptr;
+    uint32_t bar = 0;
 };
 
 // MODE kModeStep: the Euler step (M^{n+1} replaces M^n in Mt and goes to
@@ -379,7 +396,7 @@ __device__ __forceinline__ void xstep_body(const Geom& g, const LlgCoef& cf, int
                                            const float2* ta, float* Mt, float2* sb, float2* wk,
                                            const float2* __restrict__ Sh, float2* __restrict__ Snext,
                                            float* __restrict__ Mout, int* __restrict__ flag,
-                                           float* __restrict__ Mcopy = nullptr) {
+                                           float* __restrict__ Mcopy = nullptr, const XTma& xt = XTma{}) {
     using Lay = XstepLayout<N, R>;
     using F = Fft2<N>;
     constexpr int P = F::P, Q = F::Q, G = F::G, L = Lay::L, H = Lay::H, NL = Lay::NL, ZS = Lay::ZS;
@@ -401,16 +418,38 @@ __device__ __forceinline__ void xstep_body(const Geom& g, const LlgCoef& cf, int
     // s4[(c * HP + pos(kx)) * RP + pr] = rows (j0 + 2 pr, j0 + 2 pr + 1) of
     // (c, kx), pos(kx) = (kx & 1) HM + kx / 2, so that the inverse transform
     // below reads consecutive 16-byte words (every RP-th one); the RP chunks
-    // of one (c, kx) are adjacent in global memory and go to adjacent lanes
+    // of one (c, kx) are adjacent in global memory and go to adjacent lanes.
+    // With a tiled map the same layout is one box: the odd-parity position
+    // kx / 2 = HM - 1 (kx = N + 1) reads the buffer's pad plane and is never
+    // used.
+    if (xt.in) {
+        if (threadIdx.x == 0) {
+            proxy_fence_global();                          // Sh: ordinary stores of the previous kernel
+            mbar_expect_tx(xt.bar, Lay::BOX_BYTES);
+            tensor_g2s_4d(smem_addr(sb), xt.in, 2 * s_base, 0, 0, 0, xt.bar);
+        }
+        __pipeline_commit();
+        __pipeline_wait_prior(0);
+        const bool ok = mbar_wait(xt.bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                if (flag) atomicOr(flag, kFlagTimeout);
+                mbar_wait(xt.bar, 0);                      // the copy in flight lands first (bounded)
+            }
+            return;
+        }
+    } else {
 #pragma unroll
-    for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
-        const int pr = idx % RP, ck = idx / RP;
-        const int c = ck / H, kx = ck - c * H;
-        copy16(sb + ((c * HP + (kx & 1) * HM + (kx >> 1)) * RP + pr) * 2, Sh + kx * s_kx + c * s_c + s_base + 2 * pr);
+        for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
+            const int pr = idx % RP, ck = idx / RP;
+            const int c = ck / H, kx = ck - c * H;
+            copy16(sb + ((c * HP + (kx & 1) * HM + (kx >> 1)) * RP + pr) * 2,
+                   Sh + kx * s_kx + c * s_c + s_base + 2 * pr);
+        }
+        __pipeline_commit();
+        __pipeline_wait_prior(0);
+        __syncthreads();
     }
-    __pipeline_commit();
-    __pipeline_wait_prior(0);
-    __syncthreads();
 
     const int grp = threadIdx.x / G, t = threadIdx.x % G;
     const int line = grp >> 1, h = grp & 1;                 // line = c * RP + pr
@@ -553,9 +592,10 @@ __device__ __forceinline__ void xstep_body(const Geom& g, const LlgCoef& cf, int
             for (int q = 0; q < Q; ++q) wk[line * ZS + h * HOFF + t + P * q] = w[q];   // Z[2 n + h]
         }
         __syncthreads();
-        // split each pair into the two rows' half-spectra and store to Snext;
-        // the RP pairs of one (c, kx) are adjacent in global memory and go to
-        // adjacent lanes
+        // split each pair into the two rows' half-spectra and store to Snext
+        // (the RP pairs of one (c, kx) are adjacent in global memory and go
+        // to adjacent lanes), or stage them in sb, free since the inverse
+        // transform, for one tiled store
 #pragma unroll
         for (int idx = threadIdx.x; idx < 3 * H * RP; idx += T) {
             const int p2 = idx % RP, ck = idx / RP;
@@ -566,7 +606,19 @@ __device__ __forceinline__ void xstep_body(const Geom& g, const LlgCoef& cf, int
             const float2 zm = ln[(km & 1) * HOFF + (km >> 1)];
             const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y),
                                          0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-            *reinterpret_cast<float4*>(Snext + kx * s_kx + c * s_c + s_base + 2 * p2) = o;
+            if (xt.out)
+                reinterpret_cast<float4*>(sb)[(c * HP + (kx & 1) * HM + (kx >> 1)) * RP + p2] = o;
+            else
+                *reinterpret_cast<float4*>(Snext + kx * s_kx + c * s_c + s_base + 2 * p2) = o;
+        }
+        if (xt.out) {
+            proxy_fence_shared();                          // this thread's staging stores, then the copy
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tensor_s2g_4d(xt.out, 2 * s_base, 0, 0, 0, smem_addr(sb));
+                bulk_commit();
+                bulk_wait_all();                           // written before the block leaves
+            }
         }
     }
 }
@@ -615,6 +667,52 @@ __global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
     __pipeline_commit();
     pdl_wait();
     xstep_body<N, R, MODE, T>(g, cf, blockIdx.x, tw, ta, Mt, sb, wk, Sh, Snext, Mout, flag, Mcopy);
+    __syncthreads();
+    pdl_trigger();
+}
+
+// K_B with its spectrum gather (from Sh; bit 0 of `use`) and, for the step,
+// its scatter (to Snext; bit 1) as tiled tensor copies through `tin` and
+// `tout`, maps encoded for exactly those buffers (encode_xstep_maps).
+template <int N, int R, int MODE>
+__global__ void __launch_bounds__(XstepLayout<N, R>::THREADS)
+    k_xstep_tma(const __grid_constant__ Geom g, const __grid_constant__ LlgCoef cf, const float2* __restrict__ Sh,
+                float2* __restrict__ Snext, const float* __restrict__ M, float* __restrict__ Mout,
+                int* __restrict__ flag, float* __restrict__ Mcopy, const __grid_constant__ CUtensorMap tin,
+                const __grid_constant__ CUtensorMap tout, int use) {
+    using Lay = XstepLayout<N, R>;
+    using F = Fft2<N>;
+    constexpr int L = Lay::L;
+    constexpr int T = Lay::THREADS;
+    extern __shared__ __align__(128) float2 sm[];
+    float2* tw = sm + Lay::TW_OFF;
+    float2* ta = sm + Lay::TA_OFF;
+    float* Mt = reinterpret_cast<float*>(sm + Lay::MT_OFF);
+    float2* sb = sm + Lay::SB_OFF;
+    float2* wk = sm + Lay::W_OFF;
+    const uint32_t bar = smem_addr(sm + Lay::BAR_OFF);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        tensor_prefetch(&tin);
+        if (MODE == kModeStep && (use & 2)) tensor_prefetch(&tout);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = threadIdx.x; i < L / 2; i += T) copy16(tw + 2 * i, g.twx + 2 * i);
+    F::template load_ta<T>(ta, g.twx);
+    if constexpr (MODE != kModeDemag) load_mtile<N, R, T>(g, blockIdx.x, M, Mt);
+    __pipeline_commit();
+    pdl_wait();
+    // the tiled copies want the box on 128 bytes (the layout puts it there;
+    // the per-thread copies serve otherwise)
+    XTma xt;
+    if ((smem_addr(sb) & 127u) == 0) {
+        xt.in = (use & 1) ? &tin : nullptr;
+        xt.out = MODE == kModeStep && (use & 2) ? &tout : nullptr;
+        xt.bar = bar;
+    }
+    xstep_body<N, R, MODE, T>(g, cf, blockIdx.x, tw, ta, Mt, sb, wk, Sh, Snext, Mout, flag, Mcopy, xt);
     __syncthreads();
     pdl_trigger();
 }

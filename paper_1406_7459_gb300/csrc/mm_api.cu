@@ -279,9 +279,15 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
         Geom& g = c->g;
         const size_t N = (size_t)g.N;
         CU(cudaMalloc(&c->Kt, sizeof(float) * 6 * (size_t)g.Hx * g.Hy * g.Hz));
-        CU(cudaMalloc(&c->S, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
+        // the two-kernel step's spectra carry one pad kx plane (the tiled
+        // copies of the x-step touch it; nothing reads it)
+        const size_t plane = (size_t)3 * g.nz * g.Jst;
+        const size_t nS = (size_t)(g.Hx + (c->has_fs ? 1 : 0)) * plane;
+        CU(cudaMalloc(&c->S, sizeof(float2) * nS));
         if (c->has_fs) {
-            CU(cudaMalloc(&c->Sh, sizeof(float2) * (size_t)g.Hx * 3 * g.nz * g.Jst));
+            CU(cudaMalloc(&c->Sh, sizeof(float2) * nS));
+            CU(cudaMemset(c->S + (size_t)g.Hx * plane, 0, sizeof(float2) * plane));
+            CU(cudaMemset(c->Sh + (size_t)g.Hx * plane, 0, sizeof(float2) * plane));
             CU(cudaMalloc(&c->Kd, sizeof(float) * 6 * (size_t)g.Hx * kd_row(g.Hy) * g.nz));
             CU(cudaMalloc(&c->Kd0, sizeof(float) * 6 * (size_t)g.Hx * kd_row(g.Hy) * g.nz));
         }
@@ -316,6 +322,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], const double cell[3], 
             int sms = 0;
             CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
             c->fs.early = fast_step_early_trigger(g, sms);
+            encode_xstep_maps(g, &c->fs, c->Sh, c->S);   // per-thread copies where no map applies
         }
         if (c->has_persist) {
             bool usable = false;
@@ -586,6 +593,23 @@ extern "C" int mm_set_step_path(mm_ctx* c, int path) {
 extern "C" int mm_get_step_path(const mm_ctx* c) {
     if (!c) return fail(MM_EINVAL, "null context");
     return uses_persist(c) ? MM_STEP_PERSISTENT : MM_STEP_GRAPH;
+}
+
+extern "C" int mm_set_tiled_copies(mm_ctx* c, int mask) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    if (mask & ~(MM_TILED_GATHER | MM_TILED_SCATTER)) return fail(MM_EINVAL, "unknown tiled-copy bits %d", mask);
+    if (mask && !(c->has_fs && c->fs.tma))
+        return fail(MM_EUNSUPPORTED, "no tiled x-step copies for this grid");
+    if (c->fs.tma_use != mask) {
+        c->fs.tma_use = mask;
+        c->ver++;                               // re-capture the step graphs
+    }
+    return MM_OK;
+}
+
+extern "C" int mm_get_tiled_copies(const mm_ctx* c) {
+    if (!c) return fail(MM_EINVAL, "null context");
+    return c->has_fs && c->fs.tma ? c->fs.tma_use : 0;
 }
 
 extern "C" int mm_set_wait_limit(mm_ctx* c, long long polls) {

@@ -1,6 +1,7 @@
 // mm_internal.h -- context, plan and launcher declarations shared by the
 // translation units of libmm.so.  Not part of the public ABI (include/mm.h).
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only)
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -159,9 +160,25 @@ struct FastStepFns {
     // x-step kernels by Pass3Mode: demag field, effective field, Euler step
     void (*kb[3])(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*, float*) = {nullptr, nullptr,
                                                                                                nullptr};
+    // the same with the spectrum gather / scatter as tiled tensor copies
+    // (nx <= 256), through the maps below when `tma` (maps encoded) and
+    // `tma_use` (mm_set_tiled_copies) are set
+    void (*kbt[3])(Geom, LlgCoef, const float2*, float2*, const float*, float*, int*, float*, CUtensorMap,
+                   CUtensorMap, int) = {nullptr, nullptr, nullptr};
     int rb = 0, tb = 0;
     size_t sb = 0;
+    bool tma = false;
+    int tma_use = 0;                           // bit 0: tiled gather, bit 1: tiled scatter (opt-in:
+                                               // measured slower than the per-thread copies)
+    CUtensorMap tin{}, tout{};                 // gather map over tin_buf, scatter map over tout_buf
+    const float2* tin_buf = nullptr;
+    const float2* tout_buf = nullptr;
 };
+// Encode f->tin / f->tout for the x-step's gather from Sh and scatter to S
+// (each buffer one kx plane longer than the spectrum: the box's unused
+// odd-parity row falls there).  False, with f->tma cleared, where the box
+// does not fit a map (nx > 256) or the driver's encoder is unavailable.
+bool encode_xstep_maps(const Geom& g, FastStepFns* f, const float2* Sh, const float2* S);
 bool fast_step_lookup_x(int nx, FastStepFns* f);
 bool fast_step_lookup_plane_a(int ny, int nz, FastStepFns* f);
 bool fast_step_lookup_plane_b(int ny, int nz, FastStepFns* f);

@@ -26,6 +26,8 @@ MM_ELIMIT = -7
 MM_STEP_AUTO = 0
 MM_STEP_GRAPH = 1
 MM_STEP_PERSISTENT = 2
+MM_TILED_GATHER = 1
+MM_TILED_SCATTER = 2
 
 MM_INTEGRATOR_EULER = 0
 MM_INTEGRATOR_HEUN = 1
@@ -47,6 +49,8 @@ _PROTOS = {
     "mm_step_host": (_c_int, [_vp, _vp, _c_int, _c_double, _vp]),
     "mm_set_step_path": (_c_int, [_vp, _c_int]),
     "mm_get_step_path": (_c_int, [_vp]),
+    "mm_set_tiled_copies": (_c_int, [_vp, _c_int]),
+    "mm_get_tiled_copies": (_c_int, [_vp]),
     "mm_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
     "mm_run_adaptive": (_c_int, [_vp, _c_double, ctypes.POINTER(_c_double), _c_double, _c_int,
                                  ctypes.POINTER(_c_double)]),
@@ -223,6 +227,14 @@ def mm_set_step_path(ctx, path):
 
 def mm_get_step_path(ctx):
     return _check(lib().mm_get_step_path(ctx.handle))
+
+
+def mm_set_tiled_copies(ctx, mask):
+    _check(lib().mm_set_tiled_copies(ctx.handle, int(mask)))
+
+
+def mm_get_tiled_copies(ctx):
+    return _check(lib().mm_get_tiled_copies(ctx.handle))
 
 
 def mm_set_wait_limit(ctx, polls):
