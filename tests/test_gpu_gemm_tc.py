@@ -39,6 +39,12 @@ CASES = [
     ("float4 tail with beta", 130, 36, 64, False, False, 1, False, 1.0, 0.5, False),
     ("few rows, many columns (runs transposed)", 32, 4096, 32, False, False, 2, True, 1.0, 1.0, False),
     ("K = 0", 64, 32, 0, False, False, 1, False, 1.0, 2.0, False),
+    # both operands K-contiguous: the whole K resident in shared memory
+    ("K-major A and B, all of K resident", 256, 32, 256, False, True, 1, False, 1.0, 0.0, False),
+    ("K-major A and B, ragged tiles, beta", 200, 136, 48, False, True, 1, False, 1.0, 0.5, False),
+    ("K-major A and B, batched shared A, atomic", 130, 40, 64, False, True, 2, True, 0.5, 0.0, True),
+    ("K-major A and B, short K, wide N", 8192, 256, 32, False, True, 1, False, 1.0, 0.0, False),
+    ("K-major A and B, K past the resident limit", 128, 64, 288, False, True, 1, False, 1.0, 0.0, False),
 ]
 
 
