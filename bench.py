@@ -699,6 +699,67 @@ def truncation_floor(h, m):
     return float(torch.sqrt(p[..., ~keep].sum() / p.sum()))
 
 
+def run_fno(args, rank, ws):
+    """The surrogate network alone (256x256 film, width 32, 16x16 modes, 4
+    layers; random weights and inputs at the surrogate's input scale): one
+    inference forward pass (batch 1, replayed from its graph) back to back
+    and with L2 flushed before each call, and one training step (forward,
+    backward, Adam) at batch 8.  The x-mode transforms (2 per layer) run on
+    the tensor cores."""
+    import torch
+    from paper_1406_7459_gb300 import mm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    H = W = 256
+    C, m, L, Bt = 32, 16, 4, 8
+    f = mm.mm_fno_create(H, W, width=C, modes=m, layers=L, max_batch=Bt, seed=1)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x1 = 1e-2 * torch.randn(1, 3 * H * W, device="cuda", generator=g)
+    y1 = torch.empty_like(x1)
+    xt = 1e-2 * torch.randn(Bt, 3 * H * W, device="cuda", generator=g)
+    tt = torch.randn(Bt, 3 * H * W, device="cuda", generator=g)
+    K = max(10, min(args.steps, 200))
+    for _ in range(max(args.warmup, 3)):
+        mm.mm_fno_forward(f, x1, y1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        mm.mm_fno_forward(f, x1, y1)
+    e1.record()
+    torch.cuda.synchronize()
+    warm_ms = e0.elapsed_time(e1) / K
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    fl = []
+    for s in range(K):
+        flush.fill_(float(s))
+        e0.record()
+        mm.mm_fno_forward(f, x1, y1)
+        e1.record()
+        torch.cuda.synchronize()
+        fl.append(e0.elapsed_time(e1))
+    for _ in range(3):
+        mm.mm_fno_train_step(f, xt, tt, 1e-4)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(K):
+        mm.mm_fno_train_step(f, xt, tt, 1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / K
+    tc_flop = L * 2 * (2.0 * C * H * 2 * m * W)              # x-mode forward and inverse GEMMs
+    mix_flop = L * 2.0 * C * C * H * W
+    line = {"metric": "FNO forward ms (batch 1) and training step ms (batch 8)", "workload":
+            "FNO surrogate network alone, 256x256, width 32, 16x16 modes, 4 layers, BF16 / FP32 accumulate",
+            "forward_ms_back_to_back": warm_ms, "forward_ms_l2_flushed": statistics.mean(fl),
+            "train_step_ms_batch8": train_ms, "calls": K,
+            "tensor_core_gflop_per_forward": tc_flop / 1e9, "cuda_core_channel_map_gflop_per_forward": mix_flop / 1e9,
+            "data": "synthetic (random weights and inputs)"}
+    mm.mm_fno_destroy(f)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_surrogate(args, rank, ws):
     """FNO surrogate of H_demag on the 256x256x1 film (5x5x3 nm cells,
     alpha 0.02, random fields and starts): width 32, 16x16 retained modes,
@@ -862,7 +923,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="film", choices=["film", "cube", "sweep", "batch", "surrogate"],
+    ap.add_argument("--workload", default="film", choices=["film", "cube", "sweep", "batch", "surrogate", "fno"],
                     help="film: the 256x256x4 benchmark line; cube: the N^3 per-step curve; "
                          "sweep: the film size sweep; "
                          "batch: 512 uneven samples batched vs one at a time; surrogate: the FNO")
@@ -894,6 +955,8 @@ def main():
         rc = run_batch(args, rank, ws)
     elif args.workload == "surrogate":
         rc = run_surrogate(args, rank, ws)
+    elif args.workload == "fno":
+        rc = run_fno(args, rank, ws)
     else:
         rc = run_gpu(args, rank, ws)
     if ws > 1:
