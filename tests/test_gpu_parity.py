@@ -151,8 +151,9 @@ def test_graph_and_direct_launches_are_bitwise_equal(monkeypatch):
 @pytest.mark.parametrize("grid", [(32, 32, 2), (20, 12, 3)])
 def test_multi_step_graphs_are_bitwise_equal_to_direct_launches(monkeypatch, grid):
     """Runs of 37 then 16 steps: with graphs these take 16-step graphs (their
-    steps chained by programmatic launch on the two-kernel path) plus
-    single-step graphs from either parity; the states must equal launch-by-
+    steps chained by programmatic launch on the two-kernel path) plus, for
+    the remainder, direct launches on the two-kernel path and single-step
+    graphs from either parity elsewhere; the states must equal launch-by-
     launch stepping bit for bit."""
     cell = (5e-9, 5e-9, 3e-9)
     M = inputs.random_unit_m(grid, MS, seed=9)

@@ -52,9 +52,9 @@ PERSIST_GRIDS = [(256, 256, 4), (128, 128, 4), (64, 64, 4), (256, 256, 2), (256,
 
 @pytest.mark.parametrize("grid", PERSIST_GRIDS)
 def test_persistent_step_is_bitwise_the_graph_step(grid):
-    """Runs of 1, 3 and 20 steps (the graph path takes single-step graphs, a
-    16-step graph and programmatic launch chains; the persistent path one
-    launch per call) from a random start: equal bits."""
+    """Runs of 1, 3 and 20 steps (the graph path takes direct programmatic
+    launch chains for single steps and a 16-step graph; the persistent path
+    one launch per call) from a random start: equal bits."""
     mm = _mm()
     cell = (4e-9, 4e-9, 4e-9)
     M = inputs.perturbed_m(grid, MS, seed=31, amplitude=0.3)

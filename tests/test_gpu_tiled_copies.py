@@ -3,8 +3,8 @@ of the plane kernel's output and the scatter of the next spectrum as one
 4-D box per block instead of per-thread 16-byte copies and stores.
 
 The arithmetic between the copies is the same, so every mask must give the
-default path's bits: Euler steps (single-step graphs, the 16-step graph and
-programmatic launch chains), the field evaluations that end in the x-step
+default path's bits: Euler steps (direct programmatic launch chains for
+single steps, the 16-step graph), the field evaluations that end in the x-step
 kernel (H_demag, H_eff) and steps of a host-resident state.  The default
 path is pinned to the FP64 oracle by the parity tests.
 """
