@@ -29,6 +29,35 @@ struct AxisPlan {
 };
 
 __host__ __device__ __forceinline__ int padi(int e) { return e + (e >> 4); }
+
+// x / d as a multiply-high by ceil(2^32 / d): exact for 0 <= x, d < 2^16
+// (the error term x (ceil(2^32/d) d - 2^32) / 2^32 stays below 1 / d).
+struct FastDiv {
+    unsigned m;
+    int d;
+    __device__ __forceinline__ explicit FastDiv(int d_) : m(d_ > 1 ? 0xFFFFFFFFu / (unsigned)d_ + 1u : 0u), d(d_) {}
+    __device__ __forceinline__ int div(int x) const { return d > 1 ? (int)__umulhi((unsigned)x, m) : x; }
+};
+
+// The block-strided flat index t = threadIdx.x + i blockDim.x as t = q d + r,
+// advanced by next() without a division per step (any t).
+struct StrideDiv {
+    int q, r, dq, dr, d;
+    __device__ __forceinline__ explicit StrideDiv(int d_) : d(d_) {
+        q = (int)threadIdx.x / d_;
+        r = (int)threadIdx.x - q * d_;
+        dq = (int)blockDim.x / d_;
+        dr = (int)blockDim.x - dq * d_;
+    }
+    __device__ __forceinline__ void next() {
+        r += dr;
+        q += dq;
+        if (r >= d) {
+            r -= d;
+            ++q;
+        }
+    }
+};
 __host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 4) + 1; }
 
 // Complex add / subtract as one packed two-lane FP32 instruction (Blackwell
@@ -182,10 +211,14 @@ __device__ __forceinline__ void stockham_stage(const float2* src, float2* dst, i
     const int nb = L / R;
     const int total = nb * nlines;
     const int tstride = L / (Ns * R);
-    for (int g = threadIdx.x; g < total; g += blockDim.x) {
-        const int line = g / nb;
-        const int j = g - line * nb;
-        const int k = j % Ns;
+    // (line, j) of work item g = line nb + j advanced without a division per
+    // item; j / Ns by multiply-high (j, Ns < kMaxLen <= 2^16)
+    const FastDiv byNs(Ns);
+    StrideDiv w(nb);
+    for (int g = threadIdx.x; g < total; g += blockDim.x, w.next()) {
+        const int line = w.q, j = w.r;
+        const int jq = byNs.div(j);                           // j / Ns
+        const int k = j - jq * Ns;
         const float2* p = src + line * lstride;
         float2 v[R];
 #pragma unroll
@@ -198,7 +231,7 @@ __device__ __forceinline__ void stockham_stage(const float2* src, float2* dst, i
         }
         dft<R>(v);
         float2* q = dst + line * lstride;
-        const int o = (j / Ns) * Ns * R + k;
+        const int o = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             float2 a = v[r];
@@ -226,10 +259,9 @@ __device__ __forceinline__ void fft_lines(float2* buf, float2* scratch, int lstr
         const float2* src = a;
         float2* dst = scratch;
         if (P.nst & 1) {
-            for (int t = threadIdx.x; t < nl * n_in; t += blockDim.x) {
-                const int l = t / n_in, e = t - l * n_in;
-                scratch[l * lstride + padi(e)] = a[l * lstride + padi(e)];
-            }
+            StrideDiv w(n_in);
+            for (int t = threadIdx.x; t < nl * n_in; t += blockDim.x, w.next())
+                scratch[w.q * lstride + padi(w.r)] = a[w.q * lstride + padi(w.r)];
             __syncthreads();
             src = scratch;
             dst = a;

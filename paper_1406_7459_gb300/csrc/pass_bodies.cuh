@@ -21,9 +21,10 @@ __device__ __forceinline__ void pass1_body(const Geom& g, int R, int group, cons
     const int j0 = jt * R;
 
     const float* Mc = M + (size_t)c * g.N + (size_t)k * g.nx * g.ny;
-    for (int idx = threadIdx.x; idx < R * g.nx; idx += blockDim.x) {
-        const int r = idx / g.nx;
-        const int i = idx - r * g.nx;
+    StrideDiv wl(g.nx);
+    for (int idx = threadIdx.x; idx < R * g.nx; idx += blockDim.x, wl.next()) {
+        const int r = wl.q;
+        const int i = wl.r;
         const int j = j0 + r;
         const float v = (j < g.ny) ? __ldg(Mc + (size_t)j * g.nx + i) : 0.f;
         reinterpret_cast<float*>(sm + (r >> 1) * lstride + padi(i))[r & 1] = v;
@@ -32,9 +33,10 @@ __device__ __forceinline__ void pass1_body(const Geom& g, int R, int group, cons
 
     // Split Z = A + iB into the spectra of the two real rows:
     // A[k] = (Z[k] + conj Z[L-k]) / 2, B[k] = -i (Z[k] - conj Z[L-k]) / 2.
-    for (int idx = threadIdx.x; idx < g.Hx * R; idx += blockDim.x) {
-        const int r = idx % R;
-        const int kx = idx / R;
+    StrideDiv ws(R);
+    for (int idx = threadIdx.x; idx < g.Hx * R; idx += blockDim.x, ws.next()) {
+        const int r = ws.r;
+        const int kx = ws.q;
         const int j = j0 + r;
         if (j >= g.ny) continue;
         const float2* line = sm + (r >> 1) * lstride;
@@ -63,11 +65,13 @@ __device__ __forceinline__ void pass3_body(const Geom& g, int R, int group, cons
 
     // Rebuild Z = A + iB for each pair of rows (A: row 2p, B: row 2p+1) on
     // the full length Lx from the stored half-spectrum (Hermitian symmetry).
-    for (int idx = threadIdx.x; idx < 3 * g.Hx * half; idx += blockDim.x) {
-        const int rp = idx % half;
-        const int t = idx / half;
-        const int kx = t % g.Hx;
-        const int c = t / g.Hx;
+    const FastDiv byHx(g.Hx);                             // t < 3 Hx < 2^16
+    StrideDiv wr(half);
+    for (int idx = threadIdx.x; idx < 3 * g.Hx * half; idx += blockDim.x, wr.next()) {
+        const int rp = wr.r;
+        const int t = wr.q;
+        const int c = byHx.div(t);
+        const int kx = t - c * g.Hx;
         const int ja = j0 + 2 * rp;
         const float2* src = S + (((size_t)kx * 3 + c) * g.nz + k) * g.Jst;
         float2 A = (ja < g.ny) ? src[ja] : make_float2(0.f, 0.f);
@@ -81,9 +85,10 @@ __device__ __forceinline__ void pass3_body(const Geom& g, int R, int group, cons
     fft_lines(sm, sm + 3 * half * lstride, lstride, 3 * half, group, g.px, g.twx, g.Lx, true);
 
     const size_t N = (size_t)g.N;
-    for (int idx = threadIdx.x; idx < R * g.nx; idx += blockDim.x) {
-        const int r = idx / g.nx;
-        const int i = idx - r * g.nx;
+    StrideDiv wf(g.nx);
+    for (int idx = threadIdx.x; idx < R * g.nx; idx += blockDim.x, wf.next()) {
+        const int r = wf.q;
+        const int i = wf.r;
         const int j = j0 + r;
         if (j >= g.ny) {
             if (MODE == kModeStepX) {
@@ -164,11 +169,12 @@ __device__ __forceinline__ void pass3_body(const Geom& g, int R, int group, cons
         fft_lines(sm, sm + 3 * half * lstride, lstride, 3 * half, group, g.px, g.twx, g.nx, false);
         __syncthreads();
         float2* Sw = Snext;
-        for (int idx = threadIdx.x; idx < 3 * g.Hx * R; idx += blockDim.x) {
-            const int r = idx % R;
-            const int t = idx / R;
-            const int kx = t % g.Hx;
-            const int c = t / g.Hx;
+        StrideDiv wo(R);
+        for (int idx = threadIdx.x; idx < 3 * g.Hx * R; idx += blockDim.x, wo.next()) {
+            const int r = wo.r;
+            const int t = wo.q;
+            const int c = byHx.div(t);
+            const int kx = t - c * g.Hx;
             const int j = j0 + r;
             if (j >= g.ny) continue;
             const float2* line = sm + (c * half + (r >> 1)) * lstride;

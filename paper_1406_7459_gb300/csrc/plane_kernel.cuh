@@ -58,15 +58,14 @@ __device__ __forceinline__ void plane_body_multi(const Geom& g, int group, float
     const int nlt = np * nl;
     float2* plane = S + (size_t)kx0 * nl * g.Jst;
 
-    for (int idx = threadIdx.x; idx < nlt * g.ny; idx += blockDim.x) {
-        const int l = idx / g.ny;
-        const int j = idx - l * g.ny;
-        sm[l * lstride + padi(j)] = plane[(size_t)l * g.Jst + j];
-    }
+    StrideDiv wi(g.ny);
+    for (int idx = threadIdx.x; idx < nlt * g.ny; idx += blockDim.x, wi.next())
+        sm[wi.q * lstride + padi(wi.r)] = plane[(size_t)wi.q * g.Jst + wi.r];
     fft_lines(sm, sm + nlt * lstride, lstride, nlt, group, g.py, g.twy, g.ny, false);
 
-    for (int t = threadIdx.x; t < np * g.Ly; t += blockDim.x) {
-        const int pp = t / g.Ly, ky = t - pp * g.Ly;
+    StrideDiv wp(g.Ly);
+    for (int t = threadIdx.x; t < np * g.Ly; t += blockDim.x, wp.next()) {
+        const int pp = wp.q, ky = wp.r;
         const float* Kp = g.Kt + (size_t)(kx0 + pp) * g.Hz * g.Hy * 6;
         float2* sp = sm + (size_t)pp * nl * lstride;
         float2 m[3][LZ];
@@ -104,11 +103,9 @@ __device__ __forceinline__ void plane_body_multi(const Geom& g, int group, float
     }
     fft_lines(sm, sm + nlt * lstride, lstride, nlt, group, g.py, g.twy, g.Ly, true);
 
-    for (int idx = threadIdx.x; idx < nlt * g.ny; idx += blockDim.x) {
-        const int l = idx / g.ny;
-        const int j = idx - l * g.ny;
-        plane[(size_t)l * g.Jst + j] = sm[l * lstride + padi(j)];
-    }
+    StrideDiv wo(g.ny);
+    for (int idx = threadIdx.x; idx < nlt * g.ny; idx += blockDim.x, wo.next())
+        plane[(size_t)wo.q * g.Jst + wo.r] = sm[wo.q * lstride + padi(wo.r)];
 }
 
 template <int LZ>
