@@ -25,9 +25,17 @@ def _mm():
     return mm
 
 
-def test_fno_forward_and_gradients_match_fp64_oracle():
+# (H, W, width, modes, layers, batch): the fused layer tail and tiled
+# backward (widths 8, 16), their general fallbacks (width 12), odd mode
+# counts (scalar mode-mix and y-transform loads), a single layer (the last
+# layer's fused projection only), rectangular and non-multiple-of-4 films
+FNO_CASES = [(32, 32, 8, 4, 2, 2), (20, 24, 12, 3, 2, 2), (24, 18, 16, 5, 1, 3), (18, 30, 16, 4, 3, 1)]
+
+
+@pytest.mark.parametrize("case", FNO_CASES, ids=["x".join(map(str, c)) for c in FNO_CASES])
+def test_fno_forward_and_gradients_match_fp64_oracle(case):
     mm = _mm()
-    H, W, C, m, L, B = 32, 32, 8, 4, 2, 2
+    H, W, C, m, L, B = case
     f = mm.mm_fno_create(H, W, C, m, L, max_batch=B, seed=5)
     flat = mm.mm_fno_get_params(f)
     rng = np.random.default_rng(0)
