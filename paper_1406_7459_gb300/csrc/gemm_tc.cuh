@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(GemmArgs a) {
         }
         issued = true;
         if (a_vec && k0 + kTcK < a.K) load_a(k0 + kTcK);  // in flight during the MMAs
-        // one verdict for the whole CTA, so that every thread leaves the
+        // one decision for the whole CTA, so that every thread leaves the
         // loop at the same barrier
         ok = __syncthreads_and(tc_wait(mbar_s, parity) ? 1 : 0) != 0;
         parity ^= 1u;

@@ -177,7 +177,8 @@ struct FastStepFns {
 // Encode f->tin / f->tout for the x-step's gather from Sh and scatter to S
 // (each buffer one kx plane longer than the spectrum: the box's unused
 // odd-parity row falls there).  False, with f->tma cleared, where the box
-// does not fit a map (nx > 256) or the driver's encoder is unavailable.
+// does not fit a map (nx > 256) or the CUDA driver's tensor-map encoder is
+// unavailable.
 bool encode_xstep_maps(const Geom& g, FastStepFns* f, const float2* Sh, const float2* S);
 bool fast_step_lookup_x(int nx, FastStepFns* f);
 bool fast_step_lookup_plane_a(int ny, int nz, FastStepFns* f);
