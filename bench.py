@@ -382,6 +382,28 @@ def run_gpu(args, rank, ws):
     torch.cuda.synchronize()
     warm_ms = e0.elapsed_time(e1) / K
 
+    # --- context for the per-step number: what the same event pair costs
+    # around one tiny kernel after the flush, and steps timed 16 per call
+    # (L2 flushed before each call; the working set stays in L2 within it)
+    tiny = torch.zeros(1, device="cuda")
+    fa = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    fb = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for s in range(reps):
+        flush.fill_(float(s))
+        fa[s].record()
+        tiny.zero_()
+        fb[s].record()
+    torch.cuda.synchronize()
+    floor_us = 1e3 * statistics.mean(a.elapsed_time(b) for a, b in zip(fa, fb))
+    r16 = min(K, 50)
+    for s in range(r16):
+        flush.fill_(float(s))
+        fa[s].record()
+        mm.mm_step(ctx, 16, dt)
+        fb[s].record()
+    torch.cuda.synchronize()
+    call16_ms = statistics.mean(fa[s].elapsed_time(fb[s]) for s in range(r16)) / 16
+
     # --- end to end through the C ABI with host buffers
     Mh = torch.from_numpy(M0.copy()).pin_memory()
     Mo = torch.empty_like(Mh).pin_memory()
@@ -441,6 +463,10 @@ def run_gpu(args, rank, ws):
         "step_path": step_path,
         "xstep_tiled_copies": mm.mm_get_tiled_copies(ctx),
         "steady_state_l2_resident": {"ms_per_step": warm_ms, "cells_steps_per_s": ws * N / (warm_ms * 1e-3)},
+        "timing_context": {
+            "event_pair_around_tiny_kernel_after_flush_us": floor_us,
+            "flushed_16_step_calls": {"ms_per_step": call16_ms, "cells_steps_per_s": ws * N / (call16_ms * 1e-3),
+                                      "what": "L2 flushed before each mm_step(ctx, 16) call, events around the call"}},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": kbytes[dom]},
