@@ -613,7 +613,7 @@ def run_batch(args, rank, ws):
     cells = mm.mm_batch_cells(b)
     K = max(10, min(args.steps, 200))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    path_ms = {}
+    path_ms, forms = {}, {}
     for name, path in (("graph", mm.MM_STEP_GRAPH), ("persistent", mm.MM_STEP_PERSISTENT)):
         mm.mm_batch_set_path(b, path)
         mm.mm_batch_step(b, max(args.warmup, 3), dt)
@@ -626,6 +626,8 @@ def run_batch(args, rank, ws):
         barrier(ws)
         mm.mm_batch_sync(b)
         path_ms[name] = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+        forms[name] = {0: "batched kernels replayed from a CUDA graph", 1: "one cooperative launch replayed from a CUDA graph",
+                       2: "one cooperative launch issued directly"}.get(mm.mm_batch_launch_form(b), "?")
     batch_ms = path_ms["graph"]
     by = batch_bytes([s["grid"] for s in samples])
     by = {k: sum_over_ranks(float(v), ws) for k, v in by.items()}
@@ -660,7 +662,8 @@ def run_batch(args, rank, ws):
                           "paths": {name: {"ms_per_step": ms, "cells_steps_per_s": cells / (ms * 1e-3),
                                            "algorithmic_bytes_per_step": by[name],
                                            "hbm_gbs": by[name] / (ms * 1e-3) / 1e9,
-                                           "hbm_frac": by[name] / (ms * 1e-3) / 1e9 / peak}
+                                           "hbm_frac": by[name] / (ms * 1e-3) / 1e9 / peak,
+                                           "launch": forms[name]}
                                     for name, ms in path_ms.items()},
                           "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
                           "byte_model": "per sample 24N + 96X + 24Ks (plane pass; update with the next x R2C "

@@ -330,7 +330,8 @@ int mm_time_passes(mm_ctx *ctx, int reps, double dt, void *flush, unsigned long 
  * after one x transform of a new state, or (mm_batch_set_path
  * MM_STEP_PERSISTENT) as one cooperative launch for up to 1024 steps whose
  * blocks take (sample, tile) items from a work queue per pass, the passes
- * separated by bounded grid barriers (same arithmetic).
+ * separated by bounded grid barriers (same arithmetic); that launch is
+ * captured in a CUDA graph and replayed while its arguments stay the same.
  * M arrays of a batch are the samples' SoA blocks back to back (sample s
  * starts at float offset sum_{t<s} 3 N_t).
  * ------------------------------------------------------------------------ */
@@ -357,6 +358,11 @@ int mm_batch_set_path(mm_batch *b, int path);
  * up (default 2^20; 0: at once, to exercise the timeout path).  polls >= 0. */
 int mm_batch_set_wait_limit(mm_batch *b, long long polls);
 long long mm_batch_cells(const mm_batch *b);              /* total cells, or -1 */
+/* How the last mm_batch_step ran: 0 the graph step, 1 the persistent launch
+ * replayed from a CUDA graph (captured once per set of launch arguments), 2
+ * the persistent launch issued directly (the runtime refused its capture);
+ * -1 for NULL or before any step. */
+int mm_batch_launch_form(const mm_batch *b);
 /*
  * mm_batch_autotune -- time the candidate tile shapes on this batch with
  * steps of size dt, keep the fastest, and restore the state (tuning does not

@@ -7,7 +7,8 @@
 // batched kernel per pass covers the tiles of every sample, each CTA
 // finding its (sample, tile) in a prefix table over a per-sample
 // descriptor array, and the three launches of a step replay from one CUDA
-// graph.  Or (MM_STEP_PERSISTENT) one cooperative launch runs many steps:
+// graph.  Or (MM_STEP_PERSISTENT) one cooperative launch runs many steps,
+// captured once in a CUDA graph and replayed on later calls:
 // its blocks take (sample, tile) items from a work queue per pass, passes
 // separated by bounded grid barriers, the x R2C of the next step fused into
 // the update pass.  The tile shapes (rows per CTA in the x passes, threads
@@ -175,6 +176,15 @@ struct mm_batch {
     int path = MM_STEP_AUTO;
     long long wait_limit = kGridWaitLimit;
     bool spec_valid = false;                   // S holds the x spectra of the current state
+    // the persistent launch captured in a graph, for the arguments it was
+    // captured with; pgraph_ok false once a capture failed (direct launches)
+    cudaGraphExec_t pexec = nullptr;
+    int pexec_m = 0, pexec_par = 0, pexec_first = 0;
+    double pexec_dt = 0;
+    long long pexec_limit = 0;
+    unsigned long long pexec_ver = 0;
+    bool pgraph_ok = true;
+    int form = -1;                             // mm_batch_launch_form of the last step
 };
 
 #define BCU(expr)                                                                                    \
@@ -283,6 +293,7 @@ static int batch_enqueue(mm_batch* b, int par, double dt, cudaStream_t s) {
 static void batch_release(mm_batch* b) {
     for (int p = 0; p < 2; ++p)
         if (b->exec[p]) cudaGraphExecDestroy(b->exec[p]);
+    if (b->pexec) cudaGraphExecDestroy(b->pexec);
     cudaFree(b->M0);
     cudaFree(b->M1);
     cudaFree(b->S);
@@ -476,22 +487,73 @@ extern "C" int mm_batch_set_wait_limit(mm_batch* b, long long polls) {
     return MM_OK;
 }
 
+// One cooperative launch of m steps on stream s.
+static cudaError_t batch_launch_persist(const mm_batch* b, int m, double dt, int first, cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->pgrid);
+    cfg.blockDim = dim3(b->threads);
+    cfg.dynamicSmemBytes = b->psmem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_persist, (const BatchDesc*)b->d_desc, (const int*)b->d_pre, b->ns,
+                              b->tiles[0], b->tiles[1], b->tiles[2], b->par, m, (float)dt, first, b->flag, b->gb,
+                              b->wait_limit);
+}
+
+// The launch of m steps as a graph replay: captured (on the capture stream)
+// the first time and again whenever its arguments change.  A capture or
+// instantiation the runtime refuses switches the batch to direct launches.
+static cudaError_t batch_replay_persist(mm_batch* b, int m, double dt, int first) {
+    const bool same = b->pexec && b->pexec_m == m && b->pexec_dt == dt && b->pexec_par == b->par &&
+                      b->pexec_first == first && b->pexec_limit == b->wait_limit && b->pexec_ver == b->ver;
+    if (!same) {
+        if (b->pexec) {
+            cudaGraphExecDestroy(b->pexec);
+            b->pexec = nullptr;
+        }
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const cudaError_t el = batch_launch_persist(b, m, dt, first, b->cap);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->cap, &graph);
+        if (el != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return el != cudaSuccess ? el : e;
+        }
+        e = cudaGraphInstantiate(&b->pexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->pexec = nullptr;
+            return e;
+        }
+        b->pexec_m = m;
+        b->pexec_dt = dt;
+        b->pexec_par = b->par;
+        b->pexec_first = first;
+        b->pexec_limit = b->wait_limit;
+        b->pexec_ver = b->ver;
+    }
+    return cudaGraphLaunch(b->pexec, b->stream);
+}
+
 static int batch_step_persist(mm_batch* b, int n, double dt) {
     for (int s = 0; s < n;) {
         const int m = n - s < kBatchChunk ? n - s : kBatchChunk;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(b->pgrid);
-        cfg.blockDim = dim3(b->threads);
-        cfg.dynamicSmemBytes = b->psmem;
-        cfg.stream = b->stream;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        BCU(cudaLaunchKernelEx(&cfg, k_batch_persist, (const BatchDesc*)b->d_desc, (const int*)b->d_pre, b->ns,
-                               b->tiles[0], b->tiles[1], b->tiles[2], b->par, m, (float)dt, b->spec_valid ? 0 : 1,
-                               b->flag, b->gb, b->wait_limit));
+        const int first = b->spec_valid ? 0 : 1;
+        cudaError_t e = cudaErrorNotSupported;
+        if (b->pgraph_ok) {
+            e = batch_replay_persist(b, m, dt, first);
+            if (e != cudaSuccess) {
+                cudaGetLastError();                       // a refused capture leaves no sticky error
+                b->pgraph_ok = false;
+            }
+        }
+        if (e != cudaSuccess) BCU(batch_launch_persist(b, m, dt, first, b->stream));
+        b->form = e == cudaSuccess ? 1 : 2;
         b->par = (b->par + m) & 1;
         b->spec_valid = true;
         s += m;
@@ -532,6 +594,7 @@ extern "C" int mm_batch_step(mm_batch* b, int n, double dt) {
             b->exec_ver[p] = b->ver;
         }
         BCU(cudaGraphLaunch(b->exec[p], b->stream));
+        b->form = 0;
         b->par = 1 - p;
     }
     return MM_OK;
@@ -548,6 +611,8 @@ extern "C" int mm_batch_sync(mm_batch* b) {
 }
 
 extern "C" long long mm_batch_cells(const mm_batch* b) { return b ? b->cells : -1; }
+
+extern "C" int mm_batch_launch_form(const mm_batch* b) { return b ? b->form : -1; }
 
 extern "C" int mm_batch_autotune(mm_batch* b, double dt, int choice[4], float* ms_out) {
     if (!b || !(dt > 0.0)) return set_error(MM_EINVAL, "null batch or dt <= 0");

@@ -76,6 +76,7 @@ _PROTOS = {
     "mm_batch_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
     "mm_batch_sync": (_c_int, [_vp]),
     "mm_batch_cells": (ctypes.c_longlong, [_vp]),
+    "mm_batch_launch_form": (_c_int, [_vp]),
     "mm_batch_autotune": (_c_int, [_vp, _c_double, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float)]),
     "mm_fno_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _c_int, _c_int, _c_int,
                                ctypes.c_ulonglong, _vp]),
@@ -377,6 +378,12 @@ def mm_batch_set_wait_limit(b, polls):
 
 def mm_batch_cells(b):
     return int(lib().mm_batch_cells(b.handle))
+
+
+def mm_batch_launch_form(b):
+    """0: graph step; 1: persistent launch replayed from a graph; 2: persistent
+    launch issued directly; -1 before any step."""
+    return int(lib().mm_batch_launch_form(b.handle))
 
 
 def mm_batch_autotune(b, dt):

@@ -146,6 +146,27 @@ def test_persistent_batch_is_bitwise_the_graph_batch():
     assert np.array_equal(a, b)
 
 
+def test_persistent_batch_replays_one_captured_launch():
+    """The persistent step is one cooperative launch per call captured in a
+    CUDA graph: calls of 3, 3, 1 and 3 steps (the second and fourth replay
+    a launch captured before, the third is captured anew) run from a graph
+    and give the bits of the graph path."""
+    from paper_1406_7459_gb300 import mm
+    samples = inputs.batch_samples(6, seed=11, nx=(16, 80), ny=(16, 32), nz=(1, 2))
+    runs = (3, 3, 1, 3)
+    b = _make(samples)
+    mm.mm_batch_set_path(b, mm.MM_STEP_PERSISTENT)
+    assert mm.mm_batch_launch_form(b) == -1
+    for n in runs:
+        mm.mm_batch_step(b, n, 5e-14)
+        assert mm.mm_batch_launch_form(b) == 1
+    out = torch.empty(b.total, device="cuda")
+    mm.mm_batch_get_m(b, out)
+    mm.mm_batch_sync(b)
+    ref = _run_path(samples, mm.MM_STEP_GRAPH, runs)
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
 def test_persistent_full_batch_workload_is_bitwise_the_graph_batch():
     """The benchmarked 512-sample batch, autotuned, four steps both ways."""
     from paper_1406_7459_gb300 import mm
