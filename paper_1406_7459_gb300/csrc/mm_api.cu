@@ -669,21 +669,30 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
 // host memory coherently (cudaDevAttrPageableMemoryAccess, e.g. over a
 // cache-coherent chip-to-chip link), the address itself; nullptr otherwise
 // (the caller then stages the data with copies).
-static void* kernel_view(void* p) {
+// What a caller's pointer is, from one attribute query: device (or managed)
+// memory, and for host memory the address kernels may use for it (nullptr
+// when they cannot reach it).
+struct PtrKind {
+    bool device = false;
+    void* view = nullptr;
+};
+static PtrKind ptr_kind(void* p) {
+    PtrKind k;
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return nullptr;
+        return k;
     }
-    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    k.device = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) k.view = a.devicePointer;
     if (a.type == cudaMemoryTypeUnregistered) {
         int dev = 0, pageable = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess && pageable)
-            return p;
+            k.view = p;
         cudaGetLastError();
     }
-    return nullptr;
+    return k;
 }
 
 extern "C" int mm_step_host(mm_ctx* c, const float* M_in, int n, double dt, float* M_out) {
@@ -691,8 +700,9 @@ extern "C" int mm_step_host(mm_ctx* c, const float* M_in, int n, double dt, floa
     if (n < 0) return fail(MM_EINVAL, "n must be >= 0");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
     const size_t bytes = sizeof(float) * 3 * (size_t)c->g.N;
-    const bool fast = c->has_fs && c->method == MM_INTEGRATOR_EULER && !uses_persist(c) && n > 0 &&
-                      !is_device_ptr(M_in) && !is_device_ptr(M_out);
+    const PtrKind kin = ptr_kind(const_cast<float*>(M_in)), kout = ptr_kind(M_out);
+    const bool fast = c->has_fs && c->method == MM_INTEGRATOR_EULER && !uses_persist(c) && n > 0 && !kin.device &&
+                      !kout.device;
     if (!fast) {
         // copies around the ordinary step, one synchronisation at the end
         CU(cudaMemcpyAsync(c->Mbuf[c->cur], M_in, bytes, cudaMemcpyDefault, c->stream));
@@ -704,8 +714,8 @@ extern "C" int mm_step_host(mm_ctx* c, const float* M_in, int n, double dt, floa
         CU(cudaStreamSynchronize(c->stream));
         return MM_OK;
     }
-    const float* in = (const float*)kernel_view(const_cast<float*>(M_in));
-    float* out = (float*)kernel_view(M_out);
+    const float* in = (const float*)kin.view;
+    float* out = (float*)kout.view;
     if (!in) {
         CU(cudaMemcpyAsync(c->Mbuf[c->cur], M_in, bytes, cudaMemcpyHostToDevice, c->stream));
         in = c->Mbuf[c->cur];
