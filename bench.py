@@ -417,6 +417,39 @@ def run_gpu(args, rank, ws):
         # pinned input over the host link, its last writes the result back
         mm.mm_step_host(ctx, Mh, 1, dt, Mo)
         e2e_t += time.perf_counter() - t0
+    # where an end-to-end call's time goes (context; after the e2e leg, so
+    # that its timing is not perturbed): CUDA events on the context's stream
+    # just before and after the call against its wall clock, and the same
+    # step through device buffers
+    kb = min(K, 50)
+    span, wall, dev = [], [], []
+    Md2 = torch.empty(3 * N, device="cuda")
+    for s in range(kb):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ea.record()
+        mm.mm_step_host(ctx, Mh, 1, dt, Mo)
+        eb.record()
+        wall.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        span.append(ea.elapsed_time(eb) * 1e-3)
+    Mdev = torch.from_numpy(M0.copy()).cuda()
+    for s in range(kb):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mm.mm_set_m(ctx, Mdev)
+        mm.mm_step(ctx, 1, dt)
+        mm.mm_get_m(ctx, Md2)
+        mm.mm_sync(ctx)
+        dev.append(time.perf_counter() - t0)
+    e2e_breakdown = {"calls": kb, "wall_us_median": 1e6 * statistics.median(wall),
+                     "event_span_us_median": 1e6 * statistics.median(span),
+                     "device_buffers_call_us_median": 1e6 * statistics.median(dev),
+                     "what": "one mm_step_host call: wall clock, and CUDA events on its stream around it; "
+                             "device buffers: mm_set_m + mm_step + mm_get_m + mm_sync from device memory"}
     clocks = sampler.stop()
 
     t_max = max_over_ranks(t_local, ws)
@@ -474,6 +507,7 @@ def run_gpu(args, rank, ws):
         "clocks": clocks,
         "e2e": {"value": ws * N * ke / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N},
+        "e2e_breakdown": e2e_breakdown,
     }
     cb = line["compulsory_bytes"]
     cb["frac_at_step_time"] = cb["bytes"] / (step_ms_mean * 1e-3) / 1e9 / peak

@@ -38,6 +38,8 @@ def test_bench_quick_line_has_the_contract_keys():
     assert e2e["h2d_bytes_per_step"] == 12 * 262144 and e2e["d2h_bytes_per_step"] == 12 * 262144
     assert d["gpu_launches"] == 2 * 5
     assert d["demag_evals_per_s"] > 0
+    bd = d["e2e_breakdown"]
+    assert 0 < bd["event_span_us_median"] <= bd["wall_us_median"] and bd["device_buffers_call_us_median"] > 0
     tc = d["timing_context"]
     assert tc["event_pair_around_tiny_kernel_after_flush_us"] > 0
     assert tc["flushed_16_step_calls"]["ms_per_step"] > 0
