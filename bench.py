@@ -158,6 +158,7 @@ class ClockSampler:
         else:
             fd, self.path = tempfile.mkstemp(prefix="mm_clocks_", suffix=".csv")
             os.close(fd)
+        self.fh = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
@@ -165,6 +166,10 @@ class ClockSampler:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if self.fh:
+                self.fh.close()
+            if not self.keep and os.path.exists(self.path):
+                os.remove(self.path)
 
     def stop(self):
         if self.proc is None:
